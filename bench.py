@@ -1,0 +1,326 @@
+"""Benchmark of the MCLBM step on GB300: MLUPS and HBM roofline fraction.
+
+Workload (default): the 256 x 256 cavity at Ra 1e5, Pr 6.2, 3 % alumina of 30 nm, all slip
+forces, cold start. One benchmark step is one pass of the whole hot path: 1000 time steps
+(stream, moments, gradients, slip forces, drag, collision, store; graph-captured launches)
+followed by the reductions (hot/cold Nusselt numbers, component masses, residual). L2 is
+flushed (a 256 MiB write) between benchmark steps. The 256^2 state (14 MB) is L2-resident
+inside a step, so the HBM roofline is also measured on the 1024 x 1024 cavity (Ra 1e6, 2 %,
+50 nm, 226 MB of state) and reported under "hbm_case".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): independent replicas, one cavity per GPU, no data-path collective; the
+value is the sum of all ranks' lattice updates over the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "MLUPS & HBM GB/s fraction per MCLBM step; wall time to steady Nu (1e-4)"
+UNIT = "MLUPS"
+BYTES_PER_LU = 216  # 27 FP32 populations read + 27 written per lattice-node update
+CHUNK = 1000        # time steps per benchmark step (one residual / Nusselt check interval)
+OUR_KERNELS_PER_REDUCTION = 5  # nusselt, residual + final, mass + final
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 1024^2 roofline case, the steady-Nu run and the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reference_arm(args, ws, rank):
+    """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    w = workloads.CAVITY_256
+    s = oracle.RefSolver(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"]).init()
+    n_nodes = w["nx"] * w["ny"]
+    t0 = time.perf_counter()
+    s.step(5)
+    per = (time.perf_counter() - t0) / 5
+    chunk = max(2, min(200, int(3.0 / max(per, 1e-6))))  # about 3 s of CPU work per step
+    for _ in range(args.warmup):
+        s.step(chunk)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(chunk)
+        s.nusselt()
+    dt = time.perf_counter() - t0
+    mlups = n_nodes * chunk * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "nx": w["nx"], "ny": w["ny"],
+                                        "time_steps_per_bench_step": chunk},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": oracle.get_threads(),
+                         "kind": "oracle",
+                         "sample": "%d bench steps of %d time steps of the %s cavity" % (
+                             args.steps, chunk, w["name"])},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds=10.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    w = workloads.CAVITY_256
+    s = oracle.RefSolver(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"]).init()
+    t0 = time.perf_counter()
+    s.step(5)
+    per = (time.perf_counter() - t0) / 5
+    n = max(5, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": w["nx"] * w["ny"] * n / dt / 1e6, "unit": UNIT,
+            "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "%d time steps of the %s cavity from rest (%.1f s)" % (n, w["name"], dt)}
+
+
+def time_steps_only(cav, torch, nsteps):
+    """Average duration of one step launch: events around back-to-back graph replays."""
+    st = cav.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cav.step(nsteps)  # warm
+    st.synchronize()
+    a.record(st)
+    cav.step(nsteps)
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / nsteps
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+    import torch
+    import paper_1511_04552_gb300 as m
+    from paper_1511_04552_gb300 import build as pkg_build
+
+    pkg_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = workloads.CAVITY_256
+    nx, ny = w["nx"], w["ny"]
+    cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    cav.init()
+    st = cav.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def bench_step(ev=None):
+        if ev is not None:
+            ev[0].record(st)
+        cav.step(CHUNK)
+        if ev is not None:
+            ev[1].record(st)
+        cav.nusselt()
+        cav.residual()
+        cav.mass()
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(st)
+        for k in range(args.steps):
+            bench_step(evs[k])
+        t_end.record(st)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    step_time = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (args.steps * CHUNK)
+    if dist is not None:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    lu = nx * ny * CHUNK * args.steps
+    value = lu * ws / elapsed / 1e6
+    hbm_peak, peak_kind = peaks()
+    achieved = BYTES_PER_LU * nx * ny / step_time / 1e9
+
+    # end to end through the C ABI with host buffers: H2D warm fields, init, 1000 steps,
+    # all 8 fields and the Nusselt numbers back to the host
+    warm = torch.from_numpy(workloads.perturbed_rest_fields(nx, ny, w["phi"], seed=1)).pin_memory()
+    fields_host = torch.empty((8, ny, nx), dtype=torch.float32).pin_memory()
+    e2e_cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    for _ in range(max(1, args.warmup)):
+        e2e_cav.run_host(warm, CHUNK, 0xFF, fields_host)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_cav.run_host(warm, CHUNK, 0xFF, fields_host)
+    e2e_time = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_time = float(tt.item())
+    e2e_value = nx * ny * CHUNK * args.steps * ws / e2e_time / 1e6
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # HBM case: 1024^2, state larger than L2
+        w4 = workloads.CAVITY_1024
+        big = m.Cavity(w4["nx"], w4["ny"], w4["Ra"], w4["Pr"], w4["phi"], w4["d_p"])
+        big.init()
+        t_big = time_steps_only(big, torch, 640)
+        ach_big = BYTES_PER_LU * w4["nx"] * w4["ny"] / t_big / 1e9
+        extras["hbm_case"] = {
+            "workload": w4["name"], "mlups": w4["nx"] * w4["ny"] / t_big / 1e6,
+            "roofline": {"bound": "hbm", "achieved": ach_big, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach_big / hbm_peak, "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_launch": BYTES_PER_LU * w4["nx"] * w4["ny"],
+                         "launch_us": t_big * 1e6}}
+        del big
+        torch.cuda.empty_cache()
+        # cold start to steady Nu (1e-4 over two consecutive 1000-step checks)
+        sc = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"]).init()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = m.run_to_steady(sc, tol=1e-4, check_every=1000, consecutive=2, max_steps=400000)
+        extras["steady_nu"] = {"wall_s": time.perf_counter() - t0, "steps": res["steps"],
+                               "converged": res["converged"], "nu_hot": res["nu_hot"],
+                               "nu_cold": res["nu_cold"], "workload": w["name"]}
+        if ws == 1:
+            extras["cpu_baseline"] = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "nx": nx, "ny": ny, "Ra": w["Ra"], "Pr": w["Pr"],
+                       "phi": w["phi"], "d_p": w["d_p"], "time_steps_per_bench_step": CHUNK,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed between bench steps (256 MiB write); the 14 MB state is "
+                             "L2-resident within a bench step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "step_kernel", "bytes_per_launch": BYTES_PER_LU * nx * ny,
+                         "launch_us": step_time * 1e6},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * nx * ny * 4,
+                    "d2h_bytes_per_step": 8 * nx * ny * 4 + 16},
+            "gpu_launches": args.steps * (CHUNK + OUR_KERNELS_PER_REDUCTION),
+            "clocks": clk.summary(),
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

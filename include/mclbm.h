@@ -1,0 +1,190 @@
+/*
+ * mclbm.h -- C ABI of libmclbm.so, the GB300 (sm_103a) implementation of one time step of the
+ * twin-component lattice Boltzmann model (MCLBM) for buoyancy-driven convection of a
+ * nanosuspension in a differentially heated cavity (Savithiri, Dhar, Pattamatta, Das,
+ * arXiv:1511.04552). The step streams and collides the base-fluid and particle D2Q9
+ * populations f^w, f^p (Eq 18) and the thermal populations g (Eq 19) with the slip forces of
+ * Table 1 (Eqs 4, 6, 20) and the cavity walls of Eqs 34-36; reductions give the hot- and
+ * cold-wall Nusselt numbers, the component masses and a steady-state residual.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MCLBM_OK (0) or a negative MCLBM_E* code. Errors never abort the process;
+ *    mclbm_last_error() gives the text of the handle's latest error.
+ *  - Units: lattice units (dx = dt = 1) for everything on the lattice, SI for mclbm_props.
+ *  - Geometry: nx x ny fluid nodes, node (i, j), i = 0 next to the hot wall (left), j = 0 next
+ *    to the bottom wall; walls lie half a link outside the outer nodes. H = ny, L = nx.
+ *  - Field and state arrays: row-major [plane][ny][nx], x fastest, FP32, tightly packed.
+ *  - Memory ownership: the caller owns all device memory (one buffer handed over by
+ *    mclbm_bind, plus every input and output array) and the CUDA stream. A handle owns only
+ *    host state, two captured CUDA graphs and one private capture stream; it never allocates
+ *    device memory.
+ *  - Asynchrony: entry points marked "async" only enqueue work on the bound stream; those
+ *    marked "syncs" wait for the bound stream before returning.
+ */
+#ifndef MCLBM_H
+#define MCLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------------- */
+#define MCLBM_OK 0
+#define MCLBM_EINVAL (-1)    /* bad pointer, size, enum or alignment */
+#define MCLBM_EPARAM (-2)    /* physical parameters out of range, or a relaxation time <= 0.501 */
+#define MCLBM_ESTATE (-3)    /* call out of order (e.g. step before bind/init) */
+#define MCLBM_ECUDA (-4)     /* a CUDA runtime call failed; text in mclbm_last_error */
+#define MCLBM_EDIVERGED (-5) /* a reduction saw a non-finite value; sticky until mclbm_init */
+
+/* ---- slip-mechanism switches (Eq 6 and Table 1; buoyancy of Eq 20) ----------------------- */
+#define MCLBM_F_BROWNIAN 1u
+#define MCLBM_F_THERMOPHORESIS 2u
+#define MCLBM_F_DRAG 4u
+#define MCLBM_F_SAFFMAN 8u
+#define MCLBM_F_MAGNUS 16u
+#define MCLBM_F_GRAVITY 32u
+#define MCLBM_F_BUOYANCY 64u
+#define MCLBM_F_ALL 127u
+
+/* ---- field selectors (mclbm_fields); outputs follow ascending bit order ------------------ */
+#define MCLBM_UX 1u    /* mixture (barycentric) velocity, Eq 32 */
+#define MCLBM_UY 2u
+#define MCLBM_THETA 4u /* temperature, theta in [-1/2, 1/2], Eq 31 */
+#define MCLBM_PHI 8u   /* particle volume fraction rho^p rho_f / rho_p */
+#define MCLBM_RHO_W 16u /* base-fluid partial density (normalised by rho_f), Eq 29 */
+#define MCLBM_RHO_P 32u /* particle partial density (normalised by rho_f), Eq 29 */
+#define MCLBM_UPX 64u  /* particle-component velocity, Eq 30 */
+#define MCLBM_UPY 128u
+
+/* ---- initial states (mclbm_init) --------------------------------------------------------- */
+#define MCLBM_INIT_REST 0 /* rest, uniform phi, theta linear from +1/2 (hot) to -1/2 (cold) */
+#define MCLBM_INIT_WARM 2 /* equilibrium of caller fields [4][ny][nx]: ux, uy, theta, phi */
+
+/* ---- storage of the populations ---------------------------------------------------------- */
+#define MCLBM_STORE_F32 0
+
+/* Material and model parameters, SI units. mclbm_props_default gives water at 25 C and
+ * alumina particles (the paper prints no property values). */
+typedef struct mclbm_props {
+  double rho_f, cp_f, k_f, beta_f, mu_f; /* base fluid: kg/m^3, J/(kg K), W/(m K), 1/K, Pa s */
+  double rho_p, cp_p, k_p, beta_p;       /* particle material */
+  double T0_K;                           /* reference temperature (Eq 10b, Table 1 T) */
+  double dT_K;                           /* hot minus cold wall temperature */
+  double g;                              /* gravity, m/s^2 */
+  double l_f;                            /* base-fluid molecular mean free path d_f (Eq 10) */
+  double Ma;                             /* lattice buoyancy velocity U0 / c_s, 0 < Ma <= 0.5 */
+  uint32_t force_mask;                   /* MCLBM_F_* bits */
+  int32_t storage;                       /* MCLBM_STORE_F32 */
+} mclbm_props;
+
+/* Derived create-time constants (FP64), for inspection and tests. Ratios are suspension over
+ * base fluid (Eqs 7-11 at the initial phi); tau_* are the BGK relaxation times of Eqs 22-24;
+ * rho_w0, rho_p0 the initial partial densities; H_phys, dx, dt the SI cavity height, lattice
+ * spacing and time step; C_F converts a force density from N/m^3 to lattice units. */
+typedef struct mclbm_consts {
+  double U0, nu_w, alpha_w, G_B;
+  double rho_ratio, rhocp_ratio, beta_ratio, k_ratio, mu_ratio, Re_T;
+  double nu_ns, alpha_ns;
+  double rho_w0, rho_p0, Y_w0, Y_p0;
+  double tau_w, tau_p, tau_tw, tau_tp;
+  double H_phys, dx, dt, C_F, g_lb;
+  double mu_ns, rho_ns, k_ns, nu_ns_SI;
+  double V_p, A_p, m_p, beta_St, Kn, kstar, K_T;
+} mclbm_consts;
+
+typedef struct mclbm mclbm_t; /* opaque handle */
+
+/* Fills *p with the defaults (water / alumina, T0 298.15 K, dT 10 K, g 9.81, l_f 0.17 nm,
+ * Ma 0.1, all forces, FP32 storage). */
+void mclbm_props_default(mclbm_props *p);
+
+/* Creates a handle for an nx x ny cavity (2 <= nx, ny <= 32768) at Rayleigh number Ra and
+ * Prandtl number Pr of the base fluid, initial particle volume fraction phi in [0, 0.2) and
+ * particle diameter d_p (m). props may be NULL (defaults). Host only: derives the constants
+ * of Eqs 7-11 and 22-24 and the SI scales, and rejects any relaxation time <= 0.501 with
+ * MCLBM_EPARAM. *out receives the handle, or NULL on error. */
+int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
+                 const mclbm_props *props, mclbm_t **out);
+
+/* Releases the handle's host state, graphs and capture stream; frees no caller memory.
+ * Waits for the bound stream first. NULL is ignored. */
+void mclbm_destroy(mclbm_t *h);
+
+/* Bytes of device memory the handle needs in mclbm_bind (two time levels of the 27
+ * population planes, the residual snapshot, reduction scratch and a staging area). */
+size_t mclbm_buffer_bytes(const mclbm_t *h);
+
+/* Hands the handle a caller-owned device buffer (>= mclbm_buffer_bytes, 256-byte aligned)
+ * and the CUDA stream (cudaStream_t, may be NULL for the legacy default stream) that every
+ * later call enqueues on. The buffer must stay valid until mclbm_destroy or the next bind.
+ * Rebinding drops the state: mclbm_init must follow. Selects the current device's context. */
+int mclbm_bind(mclbm_t *h, void *dev_buf, size_t bytes, void *cuda_stream);
+
+/* Writes the initial populations (equilibria of Eqs 26-27) as the post-collision state of
+ * step 0, resets the step counter, the residual snapshot and the sticky divergence flag.
+ * mode MCLBM_INIT_REST ignores warm_dev; MCLBM_INIT_WARM reads warm_dev, a device array
+ * [4][ny][nx] FP32 of ux, uy, theta and phi (phi in [0, 1)). Async. */
+int mclbm_init(mclbm_t *h, int mode, const float *warm_dev);
+
+/* Advances n >= 0 time steps (Eqs 18-19 with the forces of Table 1 and the walls of
+ * Eqs 34-36), in captured CUDA graphs of 64 steps plus single launches. Async. */
+int mclbm_step(mclbm_t *h, int64_t n);
+
+/* Advances one time step of streaming only (no collision, no forces): a test hook for the
+ * wall rules. Async. */
+int mclbm_stream_only(mclbm_t *h);
+
+/* Writes the selected moments of the post-stream populations (the macroscopic fields the
+ * next step starts from) to dev_out, a device array [popcount(which)][ny][nx] FP32, planes
+ * in ascending bit order of which (MCLBM_UX ... MCLBM_UPY). Async. */
+int mclbm_fields(mclbm_t *h, uint32_t which, float *dev_out);
+
+/* Mean Nusselt numbers of the hot (left) and cold (right) walls: k_ns/k_f times the mean
+ * over the wall of the second-order one-sided gradient of theta at the half-way wall,
+ * normalised by L = nx and dT. FP64 sums. Syncs. MCLBM_EDIVERGED if non-finite. */
+int mclbm_nusselt(mclbm_t *h, double *nu_hot, double *nu_cold);
+
+/* FP64 sums of the base-fluid and particle partial densities over the cavity (Eq 29). These
+ * are invariants of the exact method. Syncs. MCLBM_EDIVERGED if non-finite. */
+int mclbm_mass(mclbm_t *h, double *mass_w, double *mass_p);
+
+/* Steady-state residual since the previous call (or mclbm_init): K = steps in between,
+ * r = max over q in {u, theta, phi} of ||q_now - q_then||_2 / (K ||q_now||_2) (0 when K = 0),
+ * FP64 sums. Replaces the snapshot. Syncs. MCLBM_EDIVERGED if non-finite. */
+int mclbm_residual(mclbm_t *h, double *r);
+
+/* Copies the 27 population planes [27][ny][nx] FP32 (f^w_0..8, f^p_0..8, g_0..8, directions
+ * in the order of Eq 21: rest, +x, +y, -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)) between the
+ * handle's current state and a caller device array. The planes hold deviations from the
+ * initial conduction state: f^sigma_q - W_q rho_sigma0 (rho_w0, rho_p0 in mclbm_consts) and
+ * g_q - W_q theta_c(i) with theta_c(i) = 1/2 - (i + 1/2)/nx.
+ * state_set also makes the state the post-collision state of step 0. Async. */
+int mclbm_state_get(mclbm_t *h, float *dev_out);
+int mclbm_state_set(mclbm_t *h, const float *dev_in);
+
+/* End-to-end run on host buffers: copies warm_host ([4][ny][nx] FP32 host array, or NULL
+ * for the rest state) to the device, initialises, advances n steps, copies the selected
+ * fields into fields_host ([popcount(which)][ny][nx], may be NULL when which == 0) and
+ * returns both Nusselt numbers (may be NULL). Syncs. */
+int mclbm_run_host(mclbm_t *h, const float *warm_host, int64_t n, uint32_t which,
+                   float *fields_host, double *nu_hot, double *nu_cold);
+
+/* Derived constants of the handle. */
+int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);
+
+/* Time steps done since the last mclbm_init or mclbm_state_set (-1 for a NULL handle). */
+int64_t mclbm_steps_done(const mclbm_t *h);
+
+/* Text of the handle's latest error ("" if none); static text for a NULL handle. */
+const char *mclbm_last_error(const mclbm_t *h);
+
+/* Short name of a return code. */
+const char *mclbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCLBM_H */

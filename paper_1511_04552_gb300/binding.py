@@ -1,0 +1,299 @@
+"""Thin Python binding of libmclbm (include/mclbm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library. PyTorch is used for device memory and
+streams. There is no CPU fallback: if libmclbm.so is missing or cannot load, the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmclbm.so")
+
+OK, EINVAL, EPARAM, ESTATE, ECUDA, EDIVERGED = 0, -1, -2, -3, -4, -5
+F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY = (
+    1, 2, 4, 8, 16, 32, 64)
+F_ALL = 127
+UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
+INIT_REST, INIT_WARM = 0, 2
+STORE_F32 = 0
+GRAPH_STEPS = 64
+
+# every entry point declared in include/mclbm.h
+EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer_bytes",
+           "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
+           "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
+           "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
+           "mclbm_last_error", "mclbm_strerror")
+
+
+class Props(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "rho_f", "cp_f", "k_f", "beta_f", "mu_f", "rho_p", "cp_p", "k_p", "beta_p",
+        "T0_K", "dT_K", "g", "l_f", "Ma")] + [("force_mask", C.c_uint32),
+                                              ("storage", C.c_int32)]
+
+
+CONST_NAMES = (
+    "U0", "nu_w", "alpha_w", "G_B",
+    "rho_ratio", "rhocp_ratio", "beta_ratio", "k_ratio", "mu_ratio", "Re_T",
+    "nu_ns", "alpha_ns",
+    "rho_w0", "rho_p0", "Y_w0", "Y_p0",
+    "tau_w", "tau_p", "tau_tw", "tau_tp",
+    "H_phys", "dx", "dt", "C_F", "g_lb",
+    "mu_ns", "rho_ns", "k_ns", "nu_ns_SI",
+    "V_p", "A_p", "m_p", "beta_St", "Kn", "kstar", "K_T")
+
+
+class Consts(C.Structure):
+    _fields_ = [(n, C.c_double) for n in CONST_NAMES]
+
+
+class MclbmError(RuntimeError):
+    def __init__(self, code, what, detail=""):
+        super().__init__("%s returned %d (%s)%s" % (
+            what, code, _strerror(code), (": " + detail) if detail else ""))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads libmclbm.so from the package directory; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libmclbm.so is not built (run paper_1511_04552_gb300.build.build() or "
+                "__graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)
+        L.mclbm_props_default.argtypes = [C.POINTER(Props)]
+        L.mclbm_props_default.restype = None
+        L.mclbm_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.POINTER(Props), C.POINTER(vp)]
+        L.mclbm_destroy.argtypes = [vp]
+        L.mclbm_destroy.restype = None
+        L.mclbm_buffer_bytes.argtypes = [vp]
+        L.mclbm_buffer_bytes.restype = C.c_size_t
+        L.mclbm_bind.argtypes = [vp, vp, C.c_size_t, vp]
+        L.mclbm_init.argtypes = [vp, C.c_int, vp]
+        L.mclbm_step.argtypes = [vp, C.c_int64]
+        L.mclbm_stream_only.argtypes = [vp]
+        L.mclbm_fields.argtypes = [vp, C.c_uint32, vp]
+        L.mclbm_nusselt.argtypes = [vp, dp, dp]
+        L.mclbm_mass.argtypes = [vp, dp, dp]
+        L.mclbm_residual.argtypes = [vp, dp]
+        L.mclbm_state_get.argtypes = [vp, vp]
+        L.mclbm_state_set.argtypes = [vp, vp]
+        L.mclbm_run_host.argtypes = [vp, fp, C.c_int64, C.c_uint32, fp, dp, dp]
+        L.mclbm_get_consts.argtypes = [vp, C.POINTER(Consts)]
+        L.mclbm_steps_done.argtypes = [vp]
+        L.mclbm_steps_done.restype = C.c_int64
+        L.mclbm_last_error.argtypes = [vp]
+        L.mclbm_last_error.restype = C.c_char_p
+        L.mclbm_strerror.argtypes = [C.c_int]
+        L.mclbm_strerror.restype = C.c_char_p
+        for name in ("mclbm_create", "mclbm_bind", "mclbm_init", "mclbm_step",
+                     "mclbm_stream_only", "mclbm_fields", "mclbm_nusselt", "mclbm_mass",
+                     "mclbm_residual", "mclbm_state_get", "mclbm_state_set", "mclbm_run_host",
+                     "mclbm_get_consts"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return lib().mclbm_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def props_default(**overrides) -> Props:
+    p = Props()
+    lib().mclbm_props_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def create(nx, ny, Ra, Pr, phi, d_p, props=None):
+    """mclbm_create: returns an opaque handle (c_void_p)."""
+    h = C.c_void_p()
+    rc = lib().mclbm_create(int(nx), int(ny), float(Ra), float(Pr), float(phi), float(d_p),
+                            C.byref(props) if props is not None else None, C.byref(h))
+    if rc != OK:
+        raise MclbmError(rc, "mclbm_create")
+    return h
+
+
+def get_consts(h) -> dict:
+    c = Consts()
+    rc = lib().mclbm_get_consts(h, C.byref(c))
+    if rc != OK:
+        raise MclbmError(rc, "mclbm_get_consts")
+    return {n: getattr(c, n) for n in CONST_NAMES}
+
+
+def _nfields(which):
+    return bin(int(which)).count("1")
+
+
+class Cavity:
+    """One cavity on one GPU: a libmclbm handle bound to a torch-owned device buffer and a
+    torch stream. Methods mirror the C entry points."""
+
+    def __init__(self, nx, ny, Ra, Pr, phi, d_p, props=None, device=None, stream=None,
+                 **prop_overrides):
+        import torch
+        self.torch = torch
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = dict(Ra=Ra, Pr=Pr, phi=phi, d_p=d_p)
+        p = props if props is not None else props_default()
+        for k, v in prop_overrides.items():
+            setattr(p, k, v)
+        self.props = p
+        self.device = torch.device(device if device is not None else "cuda")
+        self._h = create(nx, ny, Ra, Pr, phi, d_p, p)
+        nbytes = int(lib().mclbm_buffer_bytes(self._h))
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(lib().mclbm_bind(self._h, C.c_void_p(self.buffer.data_ptr()), nbytes,
+                                     C.c_void_p(self.stream.cuda_stream)), "mclbm_bind")
+
+    # -- plumbing
+    def _check(self, rc, what):
+        if rc != OK:
+            detail = lib().mclbm_last_error(self._h).decode(errors="replace")
+            raise MclbmError(rc, what, detail)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mclbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def consts(self) -> dict:
+        return get_consts(self._h)
+
+    def steps_done(self) -> int:
+        return int(lib().mclbm_steps_done(self._h))
+
+    # -- the C entry points
+    def init(self, mode=INIT_REST, warm=None):
+        """mclbm_init. warm: device float32 tensor [4, ny, nx] (ux, uy, theta, phi)."""
+        if warm is not None:
+            assert warm.dtype == self.torch.float32 and warm.is_cuda
+            assert tuple(warm.shape) == (4, self.ny, self.nx) and warm.is_contiguous()
+            self._warm_keepalive = warm
+            rc = lib().mclbm_init(self._h, INIT_WARM, C.c_void_p(warm.data_ptr()))
+        else:
+            rc = lib().mclbm_init(self._h, mode, None)
+        self._check(rc, "mclbm_init")
+        return self
+
+    def step(self, n=1):
+        self._check(lib().mclbm_step(self._h, int(n)), "mclbm_step")
+        return self
+
+    def stream_only(self):
+        self._check(lib().mclbm_stream_only(self._h), "mclbm_stream_only")
+        return self
+
+    def fields(self, which, out=None):
+        k = _nfields(which)
+        if out is None:
+            out = self.torch.empty((k, self.ny, self.nx), dtype=self.torch.float32,
+                                   device=self.device)
+        self._check(lib().mclbm_fields(self._h, int(which), C.c_void_p(out.data_ptr())),
+                    "mclbm_fields")
+        return out
+
+    def nusselt(self):
+        a, b = C.c_double(), C.c_double()
+        self._check(lib().mclbm_nusselt(self._h, C.byref(a), C.byref(b)), "mclbm_nusselt")
+        return a.value, b.value
+
+    def mass(self):
+        a, b = C.c_double(), C.c_double()
+        self._check(lib().mclbm_mass(self._h, C.byref(a), C.byref(b)), "mclbm_mass")
+        return a.value, b.value
+
+    def residual(self):
+        r = C.c_double()
+        self._check(lib().mclbm_residual(self._h, C.byref(r)), "mclbm_residual")
+        return r.value
+
+    def state_get(self, out=None):
+        if out is None:
+            out = self.torch.empty((27, self.ny, self.nx), dtype=self.torch.float32,
+                                   device=self.device)
+        self._check(lib().mclbm_state_get(self._h, C.c_void_p(out.data_ptr())),
+                    "mclbm_state_get")
+        return out
+
+    def state_set(self, st):
+        assert st.dtype == self.torch.float32 and st.is_cuda and st.is_contiguous()
+        assert tuple(st.shape) == (27, self.ny, self.nx)
+        self._check(lib().mclbm_state_set(self._h, C.c_void_p(st.data_ptr())), "mclbm_state_set")
+        return self
+
+    def run_host(self, warm_host, n, which=0, fields_out=None):
+        """mclbm_run_host on host arrays: returns (fields or None, nu_hot, nu_cold)."""
+        fptr = C.POINTER(C.c_float)
+        w = None
+        if warm_host is not None:
+            w = self._host_f32(warm_host)
+            assert w.numel() == 4 * self.nx * self.ny
+        out = None
+        if which:
+            out = fields_out if fields_out is not None else self.torch.empty(
+                (_nfields(which), self.ny, self.nx), dtype=self.torch.float32)
+        a, b = C.c_double(), C.c_double()
+        rc = lib().mclbm_run_host(
+            self._h, C.cast(w.data_ptr(), fptr) if w is not None else None, int(n), int(which),
+            C.cast(out.data_ptr(), fptr) if out is not None else None, C.byref(a), C.byref(b))
+        self._check(rc, "mclbm_run_host")
+        return out, a.value, b.value
+
+    def _host_f32(self, arr):
+        t = arr if isinstance(arr, self.torch.Tensor) else self.torch.from_numpy(
+            np.ascontiguousarray(arr, dtype=np.float32))
+        assert t.device.type == "cpu" and t.dtype == self.torch.float32 and t.is_contiguous()
+        return t
+
+
+def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, consecutive=2, max_steps=2_000_000):
+    """Advances until the hot-wall Nusselt number changes by at most tol (relative) between
+    `consecutive` successive checks `check_every` steps apart. Returns a dict with the step
+    count, the final Nusselt numbers, the history and whether the criterion was met."""
+    hist = []
+    prev = None
+    streak = 0
+    steps = 0
+    while steps < max_steps:
+        cav.step(check_every)
+        steps += check_every
+        nh, nc = cav.nusselt()
+        hist.append((steps, nh, nc))
+        if prev is not None and abs(nh - prev) <= tol * abs(nh):
+            streak += 1
+            if streak >= consecutive:
+                return dict(steps=steps, nu_hot=nh, nu_cold=nc, history=hist, converged=True)
+        else:
+            streak = 0
+        prev = nh
+    return dict(steps=steps, nu_hot=hist[-1][1] if hist else None,
+                nu_cold=hist[-1][2] if hist else None, history=hist, converged=False)

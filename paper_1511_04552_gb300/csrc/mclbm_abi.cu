@@ -1,0 +1,450 @@
+// extern "C" entry points of libmclbm (declared in include/mclbm.h): handle life cycle,
+// binding of caller memory, graph-captured stepping, reductions and host round trips.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mclbm_internal.h"
+
+using namespace mcl;
+
+struct mclbm {
+  int nx, ny;
+  double Ra, Pr, phi, d_p;
+  mclbm_props props;
+  mclbm_consts c;
+  StepConsts k;
+  Layout L;
+  StepConfig cfg;
+  // bound memory
+  char* buf = nullptr;
+  size_t buf_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+  float* state[2] = {nullptr, nullptr};
+  float* snap = nullptr;     // [4][ny][nx]
+  float* staging = nullptr;  // [8][ny][nx]
+  double* partials = nullptr;
+  double* red = nullptr;
+  int cur = 0;
+  bool initialised = false;
+  bool diverged = false;
+  int64_t steps = 0, snap_steps = 0;
+  // graphs of kGraphSteps steps starting from time level 0 or 1
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  char err[512] = {0};
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int fail(mclbm_t* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(mclbm_t* h, cudaError_t e, const char* where) {
+  return fail(h, MCLBM_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(h, expr)                                            \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr);   \
+  } while (0)
+
+struct Regions {
+  size_t state, snap, staging, partials, red, total;
+};
+
+Regions regions(const mclbm_t* h) {
+  Regions r;
+  const size_t n = (size_t)h->nx * h->ny;
+  size_t off = 0;
+  r.state = off;
+  off += align_up(2 * (size_t)kPlanes * h->L.plane * sizeof(float), 256);
+  r.snap = off;
+  off += align_up(4 * n * sizeof(float), 256);
+  r.staging = off;
+  off += align_up(8 * n * sizeof(float), 256);
+  r.partials = off;
+  off += align_up((size_t)kMaxRedBlocks * kRedWidth * sizeof(double), 256);
+  r.red = off;
+  off += align_up((size_t)kRedWidth * sizeof(double), 256);
+  r.total = off;
+  return r;
+}
+
+int ready(mclbm_t* h, bool need_init) {
+  if (!h) return MCLBM_EINVAL;
+  if (!h->buf) return fail(h, MCLBM_ESTATE, "no device buffer bound (call mclbm_bind)");
+  if (need_init && !h->initialised)
+    return fail(h, MCLBM_ESTATE, "state not initialised (call mclbm_init or mclbm_state_set)");
+  int dev = -1;
+  CK(h, cudaGetDevice(&dev));
+  if (dev != h->device) CK(h, cudaSetDevice(h->device));
+  return MCLBM_OK;
+}
+
+void drop_graphs(mclbm_t* h) {
+  for (int p = 0; p < 2; ++p)
+    if (h->graph[p]) {
+      cudaGraphExecDestroy(h->graph[p]);
+      h->graph[p] = nullptr;
+    }
+}
+
+StepArgs step_args(const mclbm_t* h, int from) {
+  StepArgs a;
+  a.src = h->state[from];
+  a.dst = h->state[1 - from];
+  a.L = h->L;
+  a.rows = h->cfg.rows;
+  a.k = h->k;
+  return a;
+}
+
+// Captures kGraphSteps alternating launches starting from time level `from`.
+int build_graph(mclbm_t* h, int from) {
+  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
+    le = launch_step(step_args(h, (from + s) & 1), h->cfg.bx, h->cap_stream);
+  cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, le, "launch_step (capture)");
+  }
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+  cudaError_t ie = cudaGraphInstantiate(&h->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    h->graph[from] = nullptr;
+    return cuda_fail(h, ie, "cudaGraphInstantiate");
+  }
+  return MCLBM_OK;
+}
+
+int d2h_sync(mclbm_t* h, void* host, const void* dev, size_t bytes) {
+  CK(h, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return MCLBM_OK;
+}
+
+int snapshot(mclbm_t* h) {
+  CK(h, launch_residual(h->state[h->cur], h->L, h->k, h->snap, false, h->partials, h->red,
+                        h->stream));
+  h->snap_steps = h->steps;
+  return MCLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mclbm_props_default(mclbm_props* p) {
+  if (p) props_default(p);
+}
+
+int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
+                 const mclbm_props* props, mclbm_t** out) {
+  if (!out) return MCLBM_EINVAL;
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nx > 32768 || ny > 32768) return MCLBM_EINVAL;
+  mclbm_props p;
+  if (props)
+    p = *props;
+  else
+    props_default(&p);
+  if (!(std::isfinite(Ra) && Ra > 0) || !(std::isfinite(Pr) && Pr > 0) ||
+      !(phi >= 0 && phi < 0.2) || !(std::isfinite(d_p) && d_p > 0))
+    return MCLBM_EPARAM;
+  const double pos[] = {p.rho_f, p.cp_f, p.k_f, p.beta_f, p.mu_f, p.rho_p, p.cp_p,
+                        p.k_p,   p.T0_K, p.dT_K, p.g,    p.l_f};
+  for (double v : pos)
+    if (!(std::isfinite(v) && v > 0)) return MCLBM_EPARAM;
+  if (!(p.beta_p >= 0) || !(p.Ma > 0 && p.Ma <= 0.5)) return MCLBM_EPARAM;
+  if (p.force_mask & ~MCLBM_F_ALL) return MCLBM_EINVAL;
+  if (p.storage != MCLBM_STORE_F32) return MCLBM_EINVAL;
+  mclbm_t* h = new (std::nothrow) mclbm();
+  if (!h) return MCLBM_EINVAL;
+  h->nx = nx;
+  h->ny = ny;
+  h->Ra = Ra;
+  h->Pr = Pr;
+  h->phi = phi;
+  h->d_p = d_p;
+  h->props = p;
+  int rc = derive_consts(nx, ny, Ra, Pr, phi, d_p, p, &h->c);
+  if (rc != MCLBM_OK) {
+    delete h;
+    return rc;
+  }
+  h->k = fold_step_consts(nx, ny, phi, d_p, p, h->c);
+  h->L.nx = nx;
+  h->L.ny = ny;
+  h->L.pitch = (int)align_up((size_t)nx, 32);
+  h->L.plane = (size_t)h->L.pitch * ny;
+  h->cfg = choose_step_config(nx, ny);
+  *out = h;
+  return MCLBM_OK;
+}
+
+void mclbm_destroy(mclbm_t* h) {
+  if (!h) return;
+  if (h->buf) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != h->device) cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+  }
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+size_t mclbm_buffer_bytes(const mclbm_t* h) { return h ? regions(h).total : 0; }
+
+int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
+  if (!h) return MCLBM_EINVAL;
+  const Regions r = regions(h);
+  if (!dev_buf) return fail(h, MCLBM_EINVAL, "device buffer is NULL");
+  if (bytes < r.total)
+    return fail(h, MCLBM_EINVAL, "buffer of %zu bytes, %zu needed", bytes, r.total);
+  if ((reinterpret_cast<uintptr_t>(dev_buf) & 255u) != 0)
+    return fail(h, MCLBM_EINVAL, "device buffer not 256-byte aligned");
+  cudaPointerAttributes at;
+  CK(h, cudaPointerGetAttributes(&at, dev_buf));
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(h, MCLBM_EINVAL, "buffer is not device memory");
+  CK(h, cudaSetDevice(at.device));
+  drop_graphs(h);
+  h->device = at.device;
+  h->buf = static_cast<char*>(dev_buf);
+  h->buf_bytes = bytes;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->state[0] = reinterpret_cast<float*>(h->buf + r.state);
+  h->state[1] = h->state[0] + (size_t)kPlanes * h->L.plane;
+  h->snap = reinterpret_cast<float*>(h->buf + r.snap);
+  h->staging = reinterpret_cast<float*>(h->buf + r.staging);
+  h->partials = reinterpret_cast<double*>(h->buf + r.partials);
+  h->red = reinterpret_cast<double*>(h->buf + r.red);
+  h->cur = 0;
+  h->initialised = false;
+  h->diverged = false;
+  h->steps = h->snap_steps = 0;
+  h->err[0] = 0;
+  return MCLBM_OK;
+}
+
+int mclbm_init(mclbm_t* h, int mode, const float* warm_dev) {
+  int rc = ready(h, false);
+  if (rc) return rc;
+  if (mode != MCLBM_INIT_REST && mode != MCLBM_INIT_WARM)
+    return fail(h, MCLBM_EINVAL, "unknown init mode %d", mode);
+  if (mode == MCLBM_INIT_WARM && !warm_dev)
+    return fail(h, MCLBM_EINVAL, "MCLBM_INIT_WARM needs warm fields");
+  h->cur = 0;
+  CK(h, launch_init(h->state[0], h->L, h->k, mode == MCLBM_INIT_WARM ? warm_dev : nullptr,
+                    h->stream));
+  h->steps = 0;
+  h->initialised = true;
+  h->diverged = false;
+  return snapshot(h);
+}
+
+int mclbm_step(mclbm_t* h, int64_t n) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (n < 0) return fail(h, MCLBM_EINVAL, "negative step count");
+  int64_t left = n;
+  while (left >= kGraphSteps) {
+    if (!h->graph[h->cur]) {
+      rc = build_graph(h, h->cur);
+      if (rc) return rc;
+    }
+    CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+    left -= kGraphSteps;  // even: the current time level is unchanged
+    h->steps += kGraphSteps;
+  }
+  for (; left > 0; --left) {
+    CK(h, launch_step(step_args(h, h->cur), h->cfg.bx, h->stream));
+    h->cur ^= 1;
+    h->steps += 1;
+  }
+  return MCLBM_OK;
+}
+
+int mclbm_stream_only(mclbm_t* h) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  CK(h, launch_stream_only(h->state[h->cur], h->state[1 - h->cur], h->L, h->k, h->stream));
+  h->cur ^= 1;
+  return MCLBM_OK;
+}
+
+int mclbm_fields(mclbm_t* h, uint32_t which, float* dev_out) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!dev_out || which == 0 || (which & ~0xFFu))
+    return fail(h, MCLBM_EINVAL, "bad field selection 0x%x or NULL output", which);
+  CK(h, launch_fields(h->state[h->cur], h->L, h->k, which, dev_out, h->stream));
+  return MCLBM_OK;
+}
+
+int mclbm_nusselt(mclbm_t* h, double* nu_hot, double* nu_cold) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!nu_hot || !nu_cold) return fail(h, MCLBM_EINVAL, "NULL output");
+  CK(h, launch_nusselt(h->state[h->cur], h->L, h->k, h->red, h->stream));
+  double s[2];
+  rc = d2h_sync(h, s, h->red, sizeof(s));
+  if (rc) return rc;
+  const double scale = h->c.k_ratio * (double)h->nx / (double)h->ny;  // L / dT, dT = 1
+  *nu_hot = s[0] * scale;
+  *nu_cold = s[1] * scale;
+  if (!std::isfinite(*nu_hot) || !std::isfinite(*nu_cold)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite Nusselt number");
+  return MCLBM_OK;
+}
+
+int mclbm_mass(mclbm_t* h, double* mass_w, double* mass_p) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!mass_w || !mass_p) return fail(h, MCLBM_EINVAL, "NULL output");
+  CK(h, launch_mass(h->state[h->cur], h->L, h->partials, h->red, h->stream));
+  double s[2];
+  rc = d2h_sync(h, s, h->red, sizeof(s));
+  if (rc) return rc;
+  const double n = (double)h->nx * h->ny;
+  *mass_w = s[0] + n * h->c.rho_w0;
+  *mass_p = s[1] + n * h->c.rho_p0;
+  if (!std::isfinite(*mass_w) || !std::isfinite(*mass_p)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite mass");
+  return MCLBM_OK;
+}
+
+int mclbm_residual(mclbm_t* h, double* r) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!r) return fail(h, MCLBM_EINVAL, "NULL output");
+  const int64_t K = h->steps - h->snap_steps;
+  CK(h, launch_residual(h->state[h->cur], h->L, h->k, h->snap, K > 0, h->partials, h->red,
+                        h->stream));
+  h->snap_steps = h->steps;
+  double res = 0.0;
+  if (K > 0) {
+    double s[6];
+    rc = d2h_sync(h, s, h->red, sizeof(s));
+    if (rc) return rc;
+    for (int g = 0; g < 3; ++g) {
+      const double num = s[2 * g], den = s[2 * g + 1];
+      double term;
+      if (num == 0.0)
+        term = 0.0;
+      else if (den == 0.0)
+        term = INFINITY;
+      else
+        term = std::sqrt(num) / ((double)K * std::sqrt(den));
+      if (term > res || std::isnan(term)) res = term;
+    }
+  } else {
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  *r = res;
+  if (std::isnan(res)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite residual");
+  return MCLBM_OK;
+}
+
+int mclbm_state_get(mclbm_t* h, float* dev_out) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!dev_out) return fail(h, MCLBM_EINVAL, "NULL output");
+  CK(h, launch_state_copy(h->state[h->cur], dev_out, h->L, true, h->stream));
+  return MCLBM_OK;
+}
+
+int mclbm_state_set(mclbm_t* h, const float* dev_in) {
+  int rc = ready(h, false);
+  if (rc) return rc;
+  if (!dev_in) return fail(h, MCLBM_EINVAL, "NULL input");
+  h->cur = 0;
+  CK(h, launch_state_copy(dev_in, h->state[0], h->L, false, h->stream));
+  h->steps = 0;
+  h->initialised = true;
+  h->diverged = false;
+  return snapshot(h);
+}
+
+int mclbm_run_host(mclbm_t* h, const float* warm_host, int64_t n, uint32_t which,
+                   float* fields_host, double* nu_hot, double* nu_cold) {
+  int rc = ready(h, false);
+  if (rc) return rc;
+  if ((which & ~0xFFu) || (which && !fields_host) || n < 0)
+    return fail(h, MCLBM_EINVAL, "bad arguments");
+  const size_t nn = (size_t)h->nx * h->ny;
+  if (warm_host) {
+    CK(h, cudaMemcpyAsync(h->staging, warm_host, 4 * nn * sizeof(float), cudaMemcpyHostToDevice,
+                          h->stream));
+    rc = mclbm_init(h, MCLBM_INIT_WARM, h->staging);
+  } else {
+    rc = mclbm_init(h, MCLBM_INIT_REST, nullptr);
+  }
+  if (rc) return rc;
+  rc = mclbm_step(h, n);
+  if (rc) return rc;
+  if (which) {
+    rc = mclbm_fields(h, which, h->staging);
+    if (rc) return rc;
+    const size_t k = (size_t)__builtin_popcount(which);
+    CK(h, cudaMemcpyAsync(fields_host, h->staging, k * nn * sizeof(float),
+                          cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (nu_hot || nu_cold) {
+    double a, b;
+    rc = mclbm_nusselt(h, &a, &b);
+    if (nu_hot) *nu_hot = a;
+    if (nu_cold) *nu_cold = b;
+    if (rc) return rc;
+  } else {
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return MCLBM_OK;
+}
+
+int mclbm_get_consts(const mclbm_t* h, mclbm_consts* out) {
+  if (!h || !out) return MCLBM_EINVAL;
+  *out = h->c;
+  return MCLBM_OK;
+}
+
+int64_t mclbm_steps_done(const mclbm_t* h) { return h ? h->steps : -1; }
+
+const char* mclbm_last_error(const mclbm_t* h) { return h ? h->err : "NULL handle"; }
+
+const char* mclbm_strerror(int code) {
+  switch (code) {
+    case MCLBM_OK: return "MCLBM_OK";
+    case MCLBM_EINVAL: return "MCLBM_EINVAL";
+    case MCLBM_EPARAM: return "MCLBM_EPARAM";
+    case MCLBM_ESTATE: return "MCLBM_ESTATE";
+    case MCLBM_ECUDA: return "MCLBM_ECUDA";
+    case MCLBM_EDIVERGED: return "MCLBM_EDIVERGED";
+    default: return "unknown";
+  }
+}
+
+}  // extern "C"

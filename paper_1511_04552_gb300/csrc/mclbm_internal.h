@@ -1,0 +1,91 @@
+// Internal declarations of libmclbm (GB300 / sm_103a). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mclbm.h"
+
+namespace mcl {
+
+constexpr int kQ = 9;        // D2Q9 directions (Eq 21)
+constexpr int kPlanes = 27;  // f^w, f^p, g
+constexpr int kGraphSteps = 64;     // steps per captured graph (even: the buffers come back)
+constexpr int kMaxRedBlocks = 304;  // reduction partials: 2 CTAs per SM on 152 SMs
+constexpr int kRedWidth = 8;        // doubles per reduction partial
+
+// FP32 constants of one step, folded on the host from the FP64 create-time constants.
+// Force coefficients turn lattice moments directly into lattice force densities.
+struct StepConsts {
+  float rho_w0, rho_p0;       // initial partial densities: offsets of the stored deviations
+  float inv_tau_w, inv_tau_p; // 1 / momentum relaxation times (Eqs 22-23)
+  float tau_tw, tau_tp;       // thermal relaxation times of the components (Eq 24)
+  float buoy;                 // (beta_ns / beta_f) G_B: buoyancy per unit rho theta (Eq 2, Eq 20)
+  float gG;                   // (1 - rho_f / rho_p) g_lb: gravity minus buoyancy per unit rho^p
+  float phi_per_rho_p;        // rho_f / rho_p: volume fraction per unit particle partial density
+  float cB;                   // Brownian: F_B = -cB rho^p (T/T0)^2 grad rho^p
+  float cT;                   // thermophoresis: F_T = -cT rho^p grad theta / (T/T0)
+  float cS;                   // Saffman: F_S = cS rho^p |u^p|^(1/2) R90(u^w - u^p)
+  float cM;                   // Magnus: F_M = cM rho^p |u^w + u^p|^2 zeta(z) n_wall
+  float t_ratio;              // dT / T0: T/T0 = 1 + theta dT / T0
+  float beta_dt;              // beta_St dt: Stokes drag rate per step
+  float cRe;                  // Re_d = cRe |u^w - u^p|
+  float two_over_ny;          // 2 z / H = two_over_ny * z_lattice
+  float inv_nx;               // 1 / nx: slope of the conduction profile theta_c
+  float th_c0;                // theta_c(0) = 1/2 - 1/(2 nx); theta_c(i) = th_c0 - i / nx
+  uint32_t mask;              // MCLBM_F_* bits
+  int has_p;                  // initial phi > 0
+  double rho_w0_d, rho_p0_d;  // FP64 offsets and rho_f / rho_p for the initial fill
+  double fr_d;
+};
+
+// Layout of the state inside the caller's buffer: 27 planes [ny][pitch] per time level.
+struct Layout {
+  int nx, ny, pitch;  // pitch: floats per row, a multiple of 32 (128 bytes)
+  size_t plane;       // floats per plane = pitch * ny
+};
+
+struct StepArgs {
+  const float* src;
+  float* dst;
+  Layout L;
+  int rows;  // rows per CTA strip
+  StepConsts k;
+};
+
+// Host-side derivation (mclbm_model.cpp).
+void props_default(mclbm_props* p);
+int derive_consts(int nx, int ny, double Ra, double Pr, double phi, double d_p,
+                  const mclbm_props& p, mclbm_consts* c);
+StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_props& p,
+                            const mclbm_consts& c);
+
+// Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
+struct StepConfig {
+  int bx;    // columns per CTA (32, 64 or 128)
+  int rows;  // rows per CTA strip
+};
+StepConfig choose_step_config(int nx, int ny);
+cudaError_t launch_step(const StepArgs& a, int bx, cudaStream_t st);
+cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
+                               cudaStream_t st);
+cudaError_t launch_init(float* dst, const Layout& L, const StepConsts& k, const float* warm,
+                        cudaStream_t st);
+cudaError_t launch_fields(const float* src, const Layout& L, const StepConsts& k, uint32_t which,
+                          float* out, cudaStream_t st);
+// Nusselt partial sums: red[0] = sum_j (8 T_h - 9 th_0 + th_1) / 3, red[1] = cold-wall twin.
+cudaError_t launch_nusselt(const float* src, const Layout& L, const StepConsts& k, double* red,
+                           cudaStream_t st);
+// Mass: red[0] = sum of f^w deviations, red[1] = sum of f^p deviations.
+cudaError_t launch_mass(const float* src, const Layout& L, double* partials, double* red,
+                        cudaStream_t st);
+// Residual sums red[0..5] = |du|^2, |u|^2, dtheta^2, theta^2, dphi^2, phi^2 against snap;
+// the snapshot [4][ny][nx] (ux, uy, theta, phi) is replaced.
+cudaError_t launch_residual(const float* src, const Layout& L, const StepConsts& k, float* snap,
+                            bool sums, double* partials, double* red, cudaStream_t st);
+cudaError_t launch_state_copy(const float* src, float* dst, const Layout& L, bool to_packed,
+                              cudaStream_t st);
+
+}  // namespace mcl

@@ -1,0 +1,654 @@
+// CUDA kernels of libmclbm for GB300 (sm_103a).
+//
+// State: 27 FP32 planes [ny][pitch] per time level (structure of arrays), f^w_0..8, f^p_0..8,
+// g_0..8 in the direction order of Eq 21. The planes hold deviations from the initial
+// conduction state: f_q - W_q rho_sigma0 and g_q - W_q theta_c(i), theta_c(i) = 1/2 - (i+1/2)/nx,
+// so the FP32 mantissa resolves the small departures that carry the flow and the heat.
+// Streaming a g deviation across x adds W_q e_qx / nx (the drop of theta_c over one link).
+//
+// The step is one fused kernel (one launch per time step): pull streaming with the wall rules
+// (Eqs 18-19 LHS, 34-36), moments (Eqs 29-32), same-time-level gradients of theta and phi,
+// the slip forces of Table 1 (Eqs 4, 6, 20), the exact drag impulse, BGK collision with
+// forcing (Eqs 18-19 RHS, 26-28, 24) and the store. A CTA owns a strip of BX columns and
+// `rows` rows and marches up it: each thread keeps its column's current row of 27 pulled
+// populations in registers while it pulls the next row, whose theta and rho^p go to a
+// 4-row ring in shared memory, so the gradients at row j see rows j-1, j, j+1 at the same
+// time level. The strip's halo rows and columns are pulled (18 planes) only for their moments.
+// No tensor cores: this is a memory-bound stencil.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mclbm_internal.h"
+
+namespace mcl {
+
+// ---- D2Q9 tables as constexpr functions (indices are compile-time after unrolling) --------
+__host__ __device__ constexpr int ex(int q) {
+  return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int q) {
+  return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int q) {
+  return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 5 + 2) % 4) + 5);
+}
+// direction mirrored in a horizontal wall: (ex, ey) -> (ex, -ey)
+__host__ __device__ constexpr int mir(int q) {
+  return q == 2 ? 4 : q == 4 ? 2 : q == 5 ? 8 : q == 8 ? 5 : q == 6 ? 7 : q == 7 ? 6 : q;
+}
+__host__ __device__ constexpr float wq(int q) {
+  return q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// Equilibrium polynomial coefficients for q = 1..8: W_q rho P_q(u) with
+// P_q = A_q e.u + B_q (e.u)^2 - C_q u.u, nominally A = 3 W, B = 4.5 W, C = 1.5 W (Eqs 26-28).
+// FP32 cannot hold 1/3 and 1/12, and rounding them independently makes the equilibrium's
+// first moment 3 (2 W_1 + 4 W_2) u = (1 + 7.5e-9) u: every collision then relaxes momentum
+// and heat flux towards a target 1e-8 too large, a bias the slow large-scale modes of a cavity
+// integrate into a ~1e-4 error. A_1 = 0.33333334 and A_2 = 0.08333333 are chosen so that
+// 2 A_1 + 4 A_2 = 1 exactly; B is exact; the rest population's equilibrium is the remainder,
+// so the zeroth moment is exact as well (up to unbiased rounding).
+__host__ __device__ constexpr float aq(int q) {
+  return q == 0 ? 0.0f : (q <= 4 ? 0x1.555556p-2f : 0x1.555554p-4f);
+}
+__host__ __device__ constexpr float bq(int q) { return q == 0 ? 0.0f : (q <= 4 ? 0.5f : 0.125f); }
+__host__ __device__ constexpr float cq(int q) {
+  return q == 0 ? 0.0f : (q <= 4 ? 1.0f / 6.0f : 1.0f / 24.0f);
+}
+static_assert(2.0f * aq(1) + 4.0f * aq(5) == 1.0f, "first moment of the equilibrium is exact");
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "axial opposites");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagonal opposites");
+static_assert(ex(opp(6)) == -ex(6) && ey(opp(6)) == -ey(6), "opposite of e_6");
+static_assert(ex(mir(5)) == ex(5) && ey(mir(5)) == -ey(5), "mirror of e_5");
+
+__device__ __forceinline__ float ldg(const float* p) { return __ldg(p); }
+
+// Pull streaming of node (i, j). FULL: all 27 populations; otherwise only f^p and g (the
+// 18 planes the halo moments need). Wall rules, in absolute values:
+//   f^w, f^p: link-wise bounce-back f_q(x) = f*_{-q}(x);
+//   g through the hot/cold wall (corners included): g_q(x) = 2 W_q T_wall - g*_{-q}(x);
+//   g through the top/bottom wall only: g_q(x) = g*_{mir q}(i - e_qx, j) (specular).
+// For the stored g deviations every rule becomes g'_q(x) = W_q e_qx s + (source deviation),
+// s = 1/nx: the interior and specular sources by the drop of theta_c over the link, the
+// isothermal walls because 2 (T_wall - theta_c) = e_qx s at the outer columns.
+template <bool FULL>
+__device__ __forceinline__ void pull_node(const float* __restrict__ src, const Layout& L, int i,
+                                          int j, float* fw, float* fp, float* g, float s) {
+  const size_t self = (size_t)j * L.pitch + i;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int si = i - ex(q), sj = j - ey(q);
+    const bool inx = (unsigned)si < (unsigned)L.nx;
+    const bool iny = (unsigned)sj < (unsigned)L.ny;
+    if (inx && iny) {
+      const size_t o = (size_t)sj * L.pitch + si;
+      if (FULL) fw[q] = ldg(src + (size_t)q * L.plane + o);
+      fp[q] = ldg(src + (size_t)(kQ + q) * L.plane + o);
+      g[q] = ldg(src + (size_t)(2 * kQ + q) * L.plane + o);
+    } else {
+      if (FULL) fw[q] = ldg(src + (size_t)opp(q) * L.plane + self);
+      fp[q] = ldg(src + (size_t)(kQ + opp(q)) * L.plane + self);
+      if (!inx) {
+        g[q] = -ldg(src + (size_t)(2 * kQ + opp(q)) * L.plane + self);
+      } else {
+        g[q] = ldg(src + (size_t)(2 * kQ + mir(q)) * L.plane + (size_t)j * L.pitch + si);
+      }
+    }
+    if (ex(q) != 0) g[q] += (float)ex(q) * wq(q) * s;
+  }
+}
+
+// theta_c(i): the linear conduction profile the g deviations are taken from
+__device__ __forceinline__ float theta_c(const StepConsts& k, int i) {
+  return k.th_c0 - (float)i * k.inv_nx;
+}
+
+struct Moments {
+  float rw, rp;    // partial density deviations from rho_w0, rho_p0
+  float mwx, mwy;  // momenta (Eq 30)
+  float mpx, mpy;
+  float th;        // theta deviation from theta_c(i) (Eq 31)
+};
+
+__device__ __forceinline__ float sum9(const float* a) {
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8];
+}
+__device__ __forceinline__ float mom_x(const float* a) {
+  return (a[1] - a[3]) + (a[5] - a[6]) + (a[8] - a[7]);
+}
+__device__ __forceinline__ float mom_y(const float* a) {
+  return (a[2] - a[4]) + (a[5] - a[8]) + (a[6] - a[7]);
+}
+
+__device__ __forceinline__ Moments moments_of(const float* fw, const float* fp, const float* g) {
+  Moments m;
+  m.rw = sum9(fw);
+  m.rp = sum9(fp);
+  m.mwx = mom_x(fw);
+  m.mwy = mom_y(fw);
+  m.mpx = mom_x(fp);
+  m.mpy = mom_y(fp);
+  m.th = sum9(g);
+  return m;
+}
+
+// Steps A2-A7 for one node: moments, forces, drag impulse, collision and store.
+// thE, thW, thN, thS and rpE, ... are the neighbours' theta and rho^p deviations (ghosts
+// already applied by the caller; theta_c's own slope -1/nx is added to d theta/dx here).
+__device__ __forceinline__ void collide_store(const StepConsts& k, const Layout& L, float* dst,
+                                              int i, int j, const float* fw, const float* fp,
+                                              const float* g, float thE, float thW, float thN,
+                                              float thS, float rpE, float rpW, float rpN,
+                                              float rpS) {
+  const Moments m = moments_of(fw, fp, g);
+  const float th = theta_c(k, i) + m.th;  // absolute temperature
+  const float rw = k.rho_w0 + m.rw;
+  const float rp = k.rho_p0 + m.rp;
+  const float rho = rw + rp;
+  const float inv_rho = 1.0f / rho;
+  const float Yw = rw * inv_rho, Yp = rp * inv_rho;
+  const float ux = (m.mwx + m.mpx) * inv_rho;  // Eq 32, barycentric
+  const float uy = (m.mwy + m.mpy) * inv_rho;
+  const float uwx = m.mwx / rw, uwy = m.mwy / rw;
+  const bool has_p = k.has_p && rp > 1e-30f;
+  const float upx = has_p ? m.mpx / rp : uwx;
+  const float upy = has_p ? m.mpy / rp : uwy;
+  const uint32_t mask = k.mask;
+
+  // external forces: Boussinesq buoyancy on the fluid, gravity pair (Eq 20, Table 1)
+  float Fbuoy = (mask & MCLBM_F_BUOYANCY) ? rho * k.buoy * th : 0.0f;
+  const bool grav = (mask & MCLBM_F_GRAVITY) != 0;
+  float Fwx = 0.0f, Fwy = 0.0f, Fpx = 0.0f, Fpy = 0.0f;
+  if (has_p) {
+    // particle-fluid interaction forces on the particle phase (reaction on the fluid)
+    float Fix = 0.0f, Fiy = 0.0f;
+    const float TT0 = 1.0f + th * k.t_ratio;  // T / T0
+    const float wx = uwx - upx, wy = uwy - upy;
+    if (mask & MCLBM_F_BROWNIAN) {
+      const float c = -k.cB * rp * TT0 * TT0 * 0.5f;
+      Fix += c * (rpE - rpW);
+      Fiy += c * (rpN - rpS);
+    }
+    if (mask & MCLBM_F_THERMOPHORESIS) {
+      const float c = -k.cT * rp / TT0;
+      Fix += c * (0.5f * (thE - thW) - k.inv_nx);
+      Fiy += c * (0.5f * (thN - thS));
+    }
+    if (mask & MCLBM_F_SAFFMAN) {
+      const float c = k.cS * rp * sqrtf(sqrtf(upx * upx + upy * upy));
+      Fix -= c * wy;
+      Fiy += c * wx;
+    }
+    if (mask & MCLBM_F_MAGNUS) {
+      // nearest wall (ties: left, right, bottom, top) and its inward normal
+      float z = (float)i + 0.5f, nrx = 1.0f, nry = 0.0f;
+      const float dr = (float)(L.nx - i) - 0.5f, db = (float)j + 0.5f;
+      const float dtp = (float)(L.ny - j) - 0.5f;
+      if (dr < z) { z = dr; nrx = -1.0f; nry = 0.0f; }
+      if (db < z) { z = db; nrx = 0.0f; nry = 1.0f; }
+      if (dtp < z) { z = dtp; nrx = 0.0f; nry = -1.0f; }
+      const float zH = z * k.two_over_ny;
+      const float sx = uwx + upx, sy = uwy + upy;
+      const float c = k.cM * rp * (sx * sx + sy * sy) * zH * (0.63f - zH);
+      Fix += c * nrx;
+      Fiy += c * nry;
+    }
+    // non-drag forces: particles F_int + F_G, fluid F_buoy + F_G0 - F_int
+    const float FGp = grav ? -rp * k.gG : 0.0f;
+    const float FG0w = grav ? k.rho_p0 * k.gG : 0.0f;
+    const float Fpnx = Fix, Fpny = Fiy + FGp;
+    const float Fwnx = -Fix, Fwny = Fbuoy + FG0w - Fiy;
+    if (mask & MCLBM_F_DRAG) {
+      // Exact drag impulse over the step (slip ODE dw/dt = -a w + b from the relaxed slip),
+      // rearranged so that the large interaction forces cancel before rounding:
+      // F^p = Y_p F_tot + mu_r [(1 - e^-a) w' - ((1 - e^-a)/a) b], F^w = F_tot - F^p.
+      const float Re = k.cRe * sqrtf(wx * wx + wy * wy);
+      const float beta = k.beta_dt * (1.0f + 0.15f * powf(Re, 0.687f));
+      const float a = beta * (1.0f + rp / rw);
+      const float E = -expm1f(-a);
+      const float Ea = (a < 1e-2f) ? 1.0f - a * (0.5f - a * (1.0f / 6.0f - a * (1.0f / 24.0f)))
+                                   : E / a;
+      const float mu_r = rw * rp * inv_rho;
+      const float relax = 1.0f - Yp * k.inv_tau_w - Yw * k.inv_tau_p;
+      const float bx = Fwnx / rw - Fpnx / rp, by = Fwny / rw - Fpny / rp;
+      // F_tot: the interaction forces cancel exactly; gravity pair = -(rho^p - rho_p0) gG
+      const float Ftx = 0.0f;
+      const float Fty = Fbuoy + (grav ? -m.rp * k.gG : 0.0f);
+      Fpx = Yp * Ftx + mu_r * (E * relax * wx - Ea * bx);
+      Fpy = Yp * Fty + mu_r * (E * relax * wy - Ea * by);
+      Fwx = Ftx - Fpx;
+      Fwy = Fty - Fpy;
+    } else {
+      Fpx = Fpnx;
+      Fpy = Fpny;
+      Fwx = Fwnx;
+      Fwy = Fwny;
+    }
+  } else {
+    Fwy = Fbuoy + (grav ? k.rho_p0 * k.gG : 0.0f);
+  }
+
+  // BGK collision with forcing 3 W_q e_q.F on the common velocity (Eqs 18, 26), in deviation
+  // form: f' <- f' + (W_q rho' + rho P_q - f') / tau + A_q e_q.F; g likewise with theta.
+  const float tau_t = Yw * k.tau_tw + Yp * k.tau_tp;  // Eq 24 with local mass fractions
+  const float inv_tau_t = 1.0f / tau_t;
+  const float usq = ux * ux + uy * uy;
+  const size_t o = (size_t)j * L.pitch + i;
+  float sw = 0.0f, sp = 0.0f, sg = 0.0f;
+#pragma unroll
+  for (int q = 1; q < kQ; ++q) {
+    const float eu = (float)ex(q) * ux + (float)ey(q) * uy;
+    const float P = eu * (aq(q) + bq(q) * eu) - cq(q) * usq;
+    const float W = wq(q);
+    const float eqw = W * m.rw + rw * P;
+    const float eqp = W * m.rp + rp * P;
+    const float eqg = W * m.th + th * P;
+    sw += eqw;
+    sp += eqp;
+    sg += eqg;
+    const float Sw = aq(q) * ((float)ex(q) * Fwx + (float)ey(q) * Fwy);
+    const float Sp = aq(q) * ((float)ex(q) * Fpx + (float)ey(q) * Fpy);
+    dst[(size_t)q * L.plane + o] = fw[q] + (eqw - fw[q]) * k.inv_tau_w + Sw;
+    dst[(size_t)(kQ + q) * L.plane + o] = fp[q] + (eqp - fp[q]) * k.inv_tau_p + Sp;
+    dst[(size_t)(2 * kQ + q) * L.plane + o] = g[q] + (eqg - g[q]) * inv_tau_t;
+  }
+  // rest populations: equilibrium = zeroth moment minus the moving equilibria
+  dst[o] = fw[0] + ((m.rw - sw) - fw[0]) * k.inv_tau_w;
+  dst[(size_t)kQ * L.plane + o] = fp[0] + ((m.rp - sp) - fp[0]) * k.inv_tau_p;
+  dst[(size_t)(2 * kQ) * L.plane + o] = g[0] + ((m.th - sg) - g[0]) * inv_tau_t;
+}
+
+// ---- the fused step ------------------------------------------------------------------------
+template <int BX>
+__global__ void __launch_bounds__(BX + 32) step_kernel(const StepArgs a) {
+  __shared__ float s_th[4][BX + 2];
+  __shared__ float s_rp[4][BX + 2];
+  const Layout L = a.L;
+  const float* __restrict__ src = a.src;
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * BX;
+  const int j0 = blockIdx.y * a.rows;
+  const int j1 = min(j0 + a.rows, L.ny);
+
+  // Role of the thread: an interior column (tid < BX) or one of the two halo columns.
+  int col = -1, sidx = 0;
+  bool interior = false;
+  if (tid < BX) {
+    col = i0 + tid;
+    sidx = tid + 1;
+    interior = true;
+  } else if (tid == BX) {
+    col = i0 - 1;
+    sidx = 0;
+  } else if (tid == BX + 1) {
+    col = i0 + BX;
+    sidx = BX + 1;
+  }
+  const bool active = col >= 0 && col < L.nx;
+
+  float fwa[kQ], fpa[kQ], ga[kQ];  // row j
+  float fwb[kQ], fpb[kQ], gb[kQ];  // row j + 1
+
+  // moments of a halo row (f^p, g only) into the ring
+  auto halo_row = [&](int r) {
+    if (active) {
+      float tw[kQ], tp[kQ], tg[kQ];
+      pull_node<false>(src, L, col, r, tw, tp, tg, a.k.inv_nx);
+      s_th[r & 3][sidx] = sum9(tg);
+      s_rp[r & 3][sidx] = sum9(tp);
+    }
+  };
+  // full pull of row r for interior threads, halo moments for halo threads
+  auto load_row = [&](int r, float* fw, float* fp, float* g) {
+    if (active) {
+      if (interior) {
+        pull_node<true>(src, L, col, r, fw, fp, g, a.k.inv_nx);
+        s_th[r & 3][sidx] = sum9(g);
+        s_rp[r & 3][sidx] = sum9(fp);
+      } else {
+        float tw[kQ];
+        pull_node<false>(src, L, col, r, tw, fp, g, a.k.inv_nx);
+        s_th[r & 3][sidx] = sum9(g);
+        s_rp[r & 3][sidx] = sum9(fp);
+      }
+    }
+  };
+  // row j: pull row j+1 into (nw, np_, ng), then finish row j from (cw, cp, cg)
+  auto body = [&](int j, const float* cw, const float* cp, const float* cg, float* nw, float* np_,
+                  float* ng) {
+    if (j + 1 < L.ny) {
+      if (j + 1 < j1)
+        load_row(j + 1, nw, np_, ng);
+      else
+        halo_row(j + 1);
+    }
+    __syncthreads();
+    if (interior && active) {
+      const int s = sidx;
+      const float th = s_th[j & 3][s], rp = s_rp[j & 3][s];
+      // theta deviations: the isothermal ghost 2 T_wall - theta is -theta' in deviation form
+      const float thW = (col > 0) ? s_th[j & 3][s - 1] : -th;
+      const float thE = (col + 1 < L.nx) ? s_th[j & 3][s + 1] : -th;
+      const float rpW = (col > 0) ? s_rp[j & 3][s - 1] : rp;
+      const float rpE = (col + 1 < L.nx) ? s_rp[j & 3][s + 1] : rp;
+      const float thS = (j > 0) ? s_th[(j - 1) & 3][s] : th;
+      const float rpS = (j > 0) ? s_rp[(j - 1) & 3][s] : rp;
+      const float thN = (j + 1 < L.ny) ? s_th[(j + 1) & 3][s] : th;
+      const float rpN = (j + 1 < L.ny) ? s_rp[(j + 1) & 3][s] : rp;
+      collide_store(a.k, L, a.dst, col, j, cw, cp, cg, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+    }
+  };
+
+  if (j0 > 0) halo_row(j0 - 1);
+  load_row(j0, fwa, fpa, ga);
+  for (int j = j0; j < j1; j += 2) {
+    body(j, fwa, fpa, ga, fwb, fpb, gb);
+    if (j + 1 < j1) body(j + 1, fwb, fpb, gb, fwa, fpa, ga);
+  }
+}
+
+// ---- streaming only (test hook) -------------------------------------------------------------
+__global__ void stream_only_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                   const Layout L, float s) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    float fw[kQ], fp[kQ], g[kQ];
+    pull_node<true>(src, L, i, j, fw, fp, g, s);
+    const size_t o = (size_t)j * L.pitch + i;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      dst[(size_t)q * L.plane + o] = fw[q];
+      dst[(size_t)(kQ + q) * L.plane + o] = fp[q];
+      dst[(size_t)(2 * kQ + q) * L.plane + o] = g[q];
+    }
+  }
+}
+
+// ---- initial equilibrium (Eqs 26-27) ---------------------------------------------------------
+__global__ void init_kernel(float* __restrict__ dst, const Layout L, const StepConsts k,
+                            const float* __restrict__ warm) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    // FP64 here (once per run) so that the stored FP32 values are correctly rounded
+    double ux = 0.0, uy = 0.0, th, drw = 0.0, drp = 0.0;
+    if (warm) {
+      ux = warm[t];
+      uy = warm[n + t];
+      th = warm[2 * n + t];
+      const double phi = warm[3 * n + t];
+      // rho^w = 1 - phi, rho^p = phi rho_p / rho_f, as deviations from the initial values
+      drw = (1.0 - phi) - k.rho_w0_d;
+      drp = phi / k.fr_d - k.rho_p0_d;
+    } else {
+      th = 0.5 - ((double)i + 0.5) / (double)L.nx;
+    }
+    const double dth = th - (0.5 - ((double)i + 0.5) / (double)L.nx);
+    const double rw = k.rho_w0_d + drw, rp = k.rho_p0_d + drp;
+    const double usq = 1.5 * (ux * ux + uy * uy);
+    const size_t o = (size_t)j * L.pitch + i;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const double eu = (double)ex(q) * ux + (double)ey(q) * uy;
+      const double P = eu * (3.0 + 4.5 * eu) - usq;
+      const double W = q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+      dst[(size_t)q * L.plane + o] = (float)(W * (drw + rw * P));
+      dst[(size_t)(kQ + q) * L.plane + o] = (float)(W * (drp + rp * P));
+      dst[(size_t)(2 * kQ + q) * L.plane + o] = (float)(W * (dth + th * P));
+    }
+  }
+}
+
+// ---- macroscopic fields of the post-stream state ----------------------------------------------
+__device__ __forceinline__ void node_fields(const StepConsts& k, const Moments& m, int i,
+                                            float* v) {
+  const float rw = k.rho_w0 + m.rw, rp = k.rho_p0 + m.rp;
+  const float rho = rw + rp;
+  v[0] = (m.mwx + m.mpx) / rho;
+  v[1] = (m.mwy + m.mpy) / rho;
+  v[2] = theta_c(k, i) + m.th;
+  v[3] = rp * k.phi_per_rho_p;
+  v[4] = rw;
+  v[5] = rp;
+  const bool has_p = k.has_p && rp > 1e-30f;
+  v[6] = has_p ? m.mpx / rp : m.mwx / rw;
+  v[7] = has_p ? m.mpy / rp : m.mwy / rw;
+}
+
+__global__ void fields_kernel(const float* __restrict__ src, const Layout L, const StepConsts k,
+                              uint32_t which, float* __restrict__ out) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    float fw[kQ], fp[kQ], g[kQ];
+    pull_node<true>(src, L, i, j, fw, fp, g, k.inv_nx);
+    float v[8];
+    node_fields(k, moments_of(fw, fp, g), i, v);
+    int slot = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (which & (1u << b)) out[(int64_t)(slot++) * n + t] = v[b];
+  }
+}
+
+// ---- deterministic FP64 block reduction -------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[N], double* out) {
+  __shared__ double s[32][N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+    for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], off);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < N; ++c) s[warp][c] = acc[c];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      double v = lane < nw ? s[lane][c] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) out[c] = v;
+    }
+  }
+}
+
+// Sums `count` partial rows of kRedWidth doubles in a fixed order into red[0..kRedWidth).
+__global__ void final_reduce_kernel(const double* __restrict__ partials, int count,
+                                    double* __restrict__ red) {
+  double acc[kRedWidth];
+#pragma unroll
+  for (int c = 0; c < kRedWidth; ++c) acc[c] = 0.0;
+  for (int r = threadIdx.x; r < count; r += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < kRedWidth; ++c) acc[c] += partials[(size_t)r * kRedWidth + c];
+  block_reduce_store<kRedWidth>(acc, red);
+}
+
+// Wall gradients from the theta deviations: with theta = theta_c + theta',
+// (8 T_h - 9 theta_0 + theta_1)/3 = 1/nx + (theta'_1 - 9 theta'_0)/3 and the cold-wall twin
+// (9 theta_{n-1} - theta_{n-2} - 8 T_c)/3 = 1/nx + (9 theta'_{n-1} - theta'_{n-2})/3.
+__global__ void nusselt_kernel(const float* __restrict__ src, const Layout L, float s,
+                               double* __restrict__ red) {
+  double acc[2] = {0.0, 0.0};
+  for (int j = threadIdx.x; j < L.ny; j += blockDim.x) {
+    float fw[kQ], fp[kQ], g[kQ];
+    pull_node<false>(src, L, 0, j, fw, fp, g, s);
+    const double t0 = sum9(g);
+    pull_node<false>(src, L, 1, j, fw, fp, g, s);
+    const double t1 = sum9(g);
+    pull_node<false>(src, L, L.nx - 1, j, fw, fp, g, s);
+    const double c0 = sum9(g);
+    pull_node<false>(src, L, L.nx - 2, j, fw, fp, g, s);
+    const double c1 = sum9(g);
+    const double slope = 1.0 / (double)L.nx;
+    acc[0] += slope + (t1 - 9.0 * t0) / 3.0;
+    acc[1] += slope + (9.0 * c0 - c1) / 3.0;
+  }
+  block_reduce_store<2>(acc, red);
+}
+
+__global__ void mass_kernel(const float* __restrict__ src, const Layout L,
+                            double* __restrict__ partials) {
+  double acc[kRedWidth];
+#pragma unroll
+  for (int c = 0; c < kRedWidth; ++c) acc[c] = 0.0;
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    const size_t o = (size_t)j * L.pitch + i;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      acc[0] += (double)ldg(src + (size_t)q * L.plane + o);
+      acc[1] += (double)ldg(src + (size_t)(kQ + q) * L.plane + o);
+    }
+  }
+  block_reduce_store<kRedWidth>(acc, partials + (size_t)blockIdx.x * kRedWidth);
+}
+
+__global__ void residual_kernel(const float* __restrict__ src, const Layout L, const StepConsts k,
+                                float* __restrict__ snap, int sums,
+                                double* __restrict__ partials) {
+  double acc[kRedWidth];
+#pragma unroll
+  for (int c = 0; c < kRedWidth; ++c) acc[c] = 0.0;
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    float fw[kQ], fp[kQ], g[kQ];
+    pull_node<true>(src, L, i, j, fw, fp, g, k.inv_nx);
+    float v[8];
+    node_fields(k, moments_of(fw, fp, g), i, v);
+    if (sums) {
+      const double now[4] = {v[0], v[1], v[2], v[3]};
+      double d[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) d[f] = now[f] - (double)snap[f * n + t];
+      acc[0] += d[0] * d[0] + d[1] * d[1];
+      acc[1] += now[0] * now[0] + now[1] * now[1];
+      acc[2] += d[2] * d[2];
+      acc[3] += now[2] * now[2];
+      acc[4] += d[3] * d[3];
+      acc[5] += now[3] * now[3];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) snap[f * n + t] = v[f];
+  }
+  if (sums) block_reduce_store<kRedWidth>(acc, partials + (size_t)blockIdx.x * kRedWidth);
+}
+
+__global__ void state_copy_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                  const Layout L, int to_packed) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  const int64_t total = n * kPlanes;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / n, r = t % n;
+    const int i = (int)(r % L.nx), j = (int)(r / L.nx);
+    const size_t po = (size_t)p * L.plane + (size_t)j * L.pitch + i;
+    if (to_packed)
+      dst[t] = src[po];
+    else
+      dst[po] = src[t];
+  }
+}
+
+// ---- launchers ------------------------------------------------------------------------------
+namespace {
+int grid_for(int64_t n, int block, int cap) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+}  // namespace
+
+StepConfig choose_step_config(int nx, int ny) {
+  StepConfig c;
+  c.bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
+  const int tiles_x = (nx + c.bx - 1) / c.bx;
+  // aim for at least ~2 CTAs per SM on 152 SMs, with strips of 4 to 32 rows
+  int rows = 32;
+  while (rows > 4 && (int64_t)tiles_x * ((ny + rows - 1) / rows) < 304) rows /= 2;
+  c.rows = rows;
+  return c;
+}
+
+cudaError_t launch_step(const StepArgs& a, int bx, cudaStream_t st) {
+  dim3 grid((a.L.nx + bx - 1) / bx, (a.L.ny + a.rows - 1) / a.rows);
+  switch (bx) {
+    case 32:
+      step_kernel<32><<<grid, 32 + 32, 0, st>>>(a);
+      break;
+    case 64:
+      step_kernel<64><<<grid, 64 + 32, 0, st>>>(a);
+      break;
+    case 128:
+      step_kernel<128><<<grid, 128 + 32, 0, st>>>(a);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
+                               cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  stream_only_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(src, dst, L, k.inv_nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(float* dst, const Layout& L, const StepConsts& k, const float* warm,
+                        cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  init_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(dst, L, k, warm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const float* src, const Layout& L, const StepConsts& k, uint32_t which,
+                          float* out, cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  fields_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(src, L, k, which, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nusselt(const float* src, const Layout& L, const StepConsts& k, double* red,
+                           cudaStream_t st) {
+  nusselt_kernel<<<1, 256, 0, st>>>(src, L, k.inv_nx, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass(const float* src, const Layout& L, double* partials, double* red,
+                        cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  const int g = grid_for(n, 256, kMaxRedBlocks);
+  mass_kernel<<<g, 256, 0, st>>>(src, L, partials);
+  final_reduce_kernel<<<1, 256, 0, st>>>(partials, g, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float* src, const Layout& L, const StepConsts& k, float* snap,
+                            bool sums, double* partials, double* red, cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny;
+  const int g = grid_for(n, 256, kMaxRedBlocks);
+  residual_kernel<<<g, 256, 0, st>>>(src, L, k, snap, sums ? 1 : 0, partials);
+  if (sums) final_reduce_kernel<<<1, 256, 0, st>>>(partials, g, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_copy(const float* src, float* dst, const Layout& L, bool to_packed,
+                              cudaStream_t st) {
+  const int64_t n = (int64_t)L.nx * L.ny * kPlanes;
+  state_copy_kernel<<<grid_for(n, 256, 8192), 256, 0, st>>>(src, dst, L, to_packed ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace mcl

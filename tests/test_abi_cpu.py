@@ -1,0 +1,104 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point declared in
+include/mclbm.h, validates its arguments, and derives the create-time constants (Eqs 7-11,
+22-24, SI scales) independently of the oracle yet to the same values."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1511_04552_gb300 import build
+    build.build()
+    import paper_1511_04552_gb300 as m
+    return m
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mclbm_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    L = pkg.lib()
+    decl = _declared()
+    assert len(decl) >= 19
+    missing = [n for n in sorted(decl) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(pkg.EXPORTS) <= decl
+
+
+def test_props_default(pkg):
+    p = pkg.props_default()
+    assert p.rho_f == 997.1 and p.rho_p == 3970.0 and p.force_mask == pkg.F_ALL
+    assert p.Ma == 0.1 and p.storage == 0
+
+
+@pytest.mark.parametrize("args", [(32, 32, 1e3, 6.2, 0.01, 20e-9), (256, 256, 1e5, 6.2, 0.03, 30e-9),
+                                  (1024, 1024, 1e6, 6.2, 0.02, 50e-9), (40, 20, 1e6, 8.923, 0.04, 33e-9),
+                                  (64, 64, 1e4, 0.71, 0.0, 10e-9), (17, 9, 3e3, 6.2, 0.19, 100e-9)])
+def test_consts_match_oracle(pkg, oracle_mod, args):
+    h = pkg.create(*args)
+    try:
+        c = pkg.get_consts(h)
+    finally:
+        pkg.lib().mclbm_destroy(h)
+    r = oracle_mod.RefSolver(*args).consts()
+    assert set(c) == set(r)
+    for k in c:
+        assert abs(c[k] - r[k]) <= 4e-15 * abs(r[k]), (k, c[k], r[k])
+
+
+@pytest.mark.parametrize("args,code", [((1, 8, 1e3, 6.2, 0.01, 2e-8), -1),
+                                       ((8, 40000, 1e3, 6.2, 0.01, 2e-8), -1),
+                                       ((8, 8, -1.0, 6.2, 0.01, 2e-8), -2),
+                                       ((8, 8, 1e3, 0.0, 0.01, 2e-8), -2),
+                                       ((8, 8, 1e3, 6.2, 0.25, 2e-8), -2),
+                                       ((8, 8, 1e3, 6.2, -0.01, 2e-8), -2),
+                                       ((8, 8, 1e3, 6.2, 0.01, 0.0), -2),
+                                       ((8, 8, 1e8, 6.2, 0.01, 2e-8), -2),
+                                       ((8, 8, float("nan"), 6.2, 0.01, 2e-8), -2)])
+def test_create_rejects(pkg, args, code):
+    with pytest.raises(pkg.MclbmError) as e:
+        pkg.create(*args)
+    assert e.value.code == code
+
+
+def test_create_rejects_bad_props(pkg):
+    for field, val, code in [("Ma", 0.0, -2), ("Ma", 0.7, -2), ("rho_p", -1.0, -2),
+                             ("force_mask", 1024, -1), ("storage", 3, -1), ("mu_f", 0.0, -2)]:
+        p = pkg.props_default(**{field: val})
+        with pytest.raises(pkg.MclbmError) as e:
+            pkg.create(16, 16, 1e3, 6.2, 0.01, 2e-8, p)
+        assert e.value.code == code, field
+
+
+def test_unbound_handle_is_refused_without_device_work(pkg):
+    L = pkg.lib()
+    h = pkg.create(16, 12, 1e3, 6.2, 0.01, 2e-8)
+    try:
+        assert L.mclbm_step(h, 1) == pkg.binding.ESTATE
+        assert L.mclbm_init(h, 0, None) == pkg.binding.ESTATE
+        a, b = C.c_double(), C.c_double()
+        assert L.mclbm_nusselt(h, C.byref(a), C.byref(b)) == pkg.binding.ESTATE
+        assert b"mclbm_bind" in L.mclbm_last_error(h)
+        assert L.mclbm_steps_done(h) == 0
+        n = L.mclbm_buffer_bytes(h)
+        assert n >= 2 * 27 * 32 * 12 * 4 + 12 * 16 * 4 * 12
+        assert L.mclbm_bind(h, None, n, None) == pkg.binding.EINVAL
+        assert L.mclbm_bind(h, C.c_void_p(256), 16, None) == pkg.binding.EINVAL
+    finally:
+        L.mclbm_destroy(h)
+    assert L.mclbm_steps_done(None) == -1
+    assert L.mclbm_last_error(None) == b"NULL handle"
+    L.mclbm_destroy(None)
+    assert L.mclbm_strerror(-5) == b"MCLBM_EDIVERGED"

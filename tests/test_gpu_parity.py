@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the same
+seeded inputs. Fields must agree to a relative L2 of 1e-5 and the Nusselt numbers to 1e-5
+relative (FP32 arithmetic against FP64)."""
+import numpy as np
+import pytest
+
+import workloads
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.ensure_built()
+
+
+def _run_pair(steps, **kw):
+    gpu, ref = P.make_pair(**kw)
+    gpu.step(steps)
+    ref.step(steps)
+    return gpu, ref
+
+
+def _assert_parity(gpu, ref, rtol=P.FIELD_RTOL, nu_rtol=P.NU_RTOL):
+    errs, bad = P.compare_fields(gpu, ref, rtol)
+    assert not bad, errs
+    gh, gc = gpu.nusselt()
+    rh, rc = ref.nusselt()
+    assert abs(gh - rh) <= nu_rtol * abs(rh), (gh, rh)
+    assert abs(gc - rc) <= nu_rtol * abs(rc), (gc, rc)
+    return errs
+
+
+@pytest.mark.parametrize("seed", [None, 1])
+def test_cavity32_2000_steps(seed):
+    """32 x 32, Ra 1e3, Pr 6.2, 1 % alumina 20 nm, all slip forces, 2000 steps."""
+    w = workloads.CAVITY_32
+    gpu, ref = _run_pair(w["steps"], nx=w["nx"], ny=w["ny"], Ra=w["Ra"], Pr=w["Pr"], phi=w["phi"],
+                         d_p=w["d_p"], seed=seed)
+    errs = _assert_parity(gpu, ref)
+    print("cavity32 seed", seed, errs)
+
+
+@pytest.mark.parametrize("nx,ny,Ra,phi,d_p,steps,mask", [
+    (37, 29, 1e4, 0.02, 30e-9, 500, 127),     # ragged against 64-column tiles and strips
+    (130, 7, 1e3, 0.01, 20e-9, 300, 127),     # two column tiles, a ragged one, few rows
+    (2, 2, 1e3, 0.01, 20e-9, 200, 127),       # every node touches two walls
+    (3, 5, 1e3, 0.04, 50e-9, 200, 127),
+    (200, 67, 1e5, 0.03, 30e-9, 400, 127),    # several tiles and strips, ragged both ways
+    (48, 40, 1e5, 0.0, 30e-9, 600, 127),      # pure fluid
+    (40, 40, 1e5, 0.03, 30e-9, 400, 4 | 8 | 16 | 64),   # no B, T, G
+    # no drag: explicit forces only (thermophoresis and gravity without drag are unstable
+    # by construction: beta dt is 1e3-1e7, which is why the drag impulse is integrated exactly)
+    # (Saffman lift without drag grows the slip without bound too)
+    (40, 40, 1e5, 0.03, 30e-9, 400, 1 | 16 | 64),
+    (33, 65, 1e4, 0.19, 100e-9, 300, 127),    # dense suspension, large particles
+])
+def test_ragged_and_masked(nx, ny, Ra, phi, d_p, steps, mask):
+    gpu, ref = _run_pair(steps, nx=nx, ny=ny, Ra=Ra, Pr=6.2, phi=phi, d_p=d_p, seed=3,
+                         force_mask=mask)
+    _assert_parity(gpu, ref)
+
+
+def test_cavity64_20000_steps():
+    gpu, ref = _run_pair(20000, nx=64, ny=64, Ra=1e5, Pr=6.2, phi=0.03, d_p=30e-9, seed=2)
+    errs = _assert_parity(gpu, ref)
+    print("cavity64", errs)
+
+
+def test_stream_only_matches_oracle_pull():
+    """Streaming with the wall rules on a random state: a permutation for f (bit-exact), and
+    g exact up to the rounding of the added conduction-profile drop."""
+    import torch
+    for nx, ny in [(5, 4), (67, 33), (130, 9), (2, 2)]:
+        gpu, ref = P.make_pair(nx, ny, 1e3, 6.2, 0.01, 20e-9)
+        c = gpu.consts()
+        dev = workloads.random_state(nx, ny, seed=nx * 100 + ny)
+        gpu.state_set(torch.from_numpy(dev).cuda())
+        ref.set_state(P.dev_to_abs(dev, c))
+        gpu.stream_only()
+        ref.stream_only()
+        g = gpu.state_get().cpu().numpy()
+        r = P.abs_to_dev(ref.get_state(), c)
+        np.testing.assert_array_equal(g[:18], r[:18].astype(np.float32))
+        np.testing.assert_allclose(g[18:], r[18:], rtol=0, atol=2.5e-7)
+
+
+@pytest.mark.parametrize("w,pre", [(workloads.CAVITY_256, 3000), (workloads.CAVITY_1024, 200)])
+def test_one_step_full_size(w, pre):
+    """At the benchmark sizes: evolve on the GPU (graph-captured launches, as timed), then one
+    more step on both sides from the identical exported state, compared plane by plane."""
+    import torch
+    import oracle
+    import paper_1511_04552_gb300 as m
+    gpu = m.Cavity(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    gpu.init()
+    gpu.step(pre)
+    st_abs = P.gpu_state_abs(gpu)
+    dev_before = gpu.state_get().clone()
+    gpu.step(1)
+    after = P.gpu_state_abs(gpu)
+    ref = oracle.RefSolver(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    ref.set_state(st_abs)
+    ref.step(1)
+    r = ref.get_state()
+    c = gpu.consts()
+    dev_ref = P.abs_to_dev(r, c)
+    dev_gpu = P.abs_to_dev(after, c)
+    for q in range(27):
+        e = P.rel_l2(dev_gpu[q], dev_ref[q])
+        assert e < 1e-5, (q, e)
+    # the input state itself survived the export unchanged
+    gpu.state_set(dev_before)
+    assert torch.equal(gpu.state_get(), dev_before)
+
+
+def test_mass_conservation_gpu():
+    w = workloads.CAVITY_32
+    gpu, ref = P.make_pair(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"], seed=1)
+    m0 = gpu.mass()
+    r0 = ref.mass()
+    assert abs(m0[0] - r0[0]) < 1e-9 * r0[0] and abs(m0[1] - r0[1]) < 1e-7 * r0[1]
+    gpu.step(2000)
+    m1 = gpu.mass()
+    assert abs(m1[0] - m0[0]) < 1e-6 * m0[0]
+    assert abs(m1[1] - m0[1]) < 1e-6 * m0[1]
+
+
+def test_conduction_limit_gpu():
+    mask = 4 | 1 | 8 | 16
+    gpu, ref = P.make_pair(24, 16, 1e3, 6.2, 0.02, 20e-9, force_mask=mask)
+    gpu.step(300)
+    k = gpu.consts()["k_ratio"]
+    nh, nc = gpu.nusselt()
+    assert abs(nh - k) < 2e-6 * k and abs(nc - k) < 2e-6 * k
+    u = gpu.fields(1 | 2).abs().max().item()
+    assert u < 1e-7
+
+
+def test_residual_matches_oracle():
+    gpu, ref = _run_pair(1000, nx=40, ny=40, Ra=1e4, Pr=6.2, phi=0.02, d_p=30e-9, seed=4)
+    rg, rr = gpu.residual(), ref.residual()
+    assert abs(rg - rr) < 1e-3 * rr, (rg, rr)
+    gpu.step(500)
+    ref.step(500)
+    rg, rr = gpu.residual(), ref.residual()
+    assert abs(rg - rr) < 1e-3 * rr, (rg, rr)
+    assert gpu.residual() == 0.0  # no steps since the last check
+
+
+def test_graph_and_single_launches_agree_bitwise():
+    import torch
+    import paper_1511_04552_gb300 as m
+    a = m.Cavity(70, 50, 1e5, 6.2, 0.03, 30e-9).init()
+    b = m.Cavity(70, 50, 1e5, 6.2, 0.03, 30e-9).init()
+    a.step(64 * 2 + 7)
+    for _ in range(64 * 2 + 7):
+        b.step(1)
+    assert a.steps_done() == b.steps_done() == 135
+    assert torch.equal(a.state_get(), b.state_get())
+
+
+def test_run_host_matches_device_path():
+    import torch
+    import paper_1511_04552_gb300 as m
+    warm = workloads.perturbed_rest_fields(48, 32, 0.02, seed=9)
+    a = m.Cavity(48, 32, 1e4, 6.2, 0.02, 30e-9)
+    f_host, nh, nc = a.run_host(warm, 777, P.ALL_FIELDS)
+    b = m.Cavity(48, 32, 1e4, 6.2, 0.02, 30e-9)
+    b.init(warm=torch.from_numpy(warm).cuda()).step(777)
+    assert torch.equal(f_host, b.fields(P.ALL_FIELDS).cpu())
+    assert (nh, nc) == b.nusselt()
+
+
+def test_nan_state_reports_divergence():
+    """A non-finite population makes the reductions that read it fail with MCLBM_EDIVERGED,
+    and the flag stays set (sticky) until the next init."""
+    import paper_1511_04552_gb300 as m
+    cav = m.Cavity(16, 16, 1e3, 6.2, 0.01, 20e-9).init()
+    for plane, (j, i), call in [(20, (5, 7), "residual"), (3, (2, 0), "mass"),
+                                (19, (9, 0), "nusselt")]:
+        cav.init()
+        cav.step(2)
+        st = cav.state_get()
+        st[plane, j, i] = float("nan")
+        cav.state_set(st)
+        cav.step(1)
+        with pytest.raises(m.MclbmError) as e:
+            getattr(cav, call)()
+        assert e.value.code == -5
+        with pytest.raises(m.MclbmError):  # sticky
+            cav.nusselt()
+    cav.init()  # clears the flag
+    assert np.isfinite(cav.nusselt()[0])
+
+
+def test_errors_with_device():
+    import torch
+    import paper_1511_04552_gb300 as m
+    cav = m.Cavity(16, 16, 1e3, 6.2, 0.01, 20e-9)
+    L = m.lib()
+    assert L.mclbm_init(cav.handle, 2, None) == -1  # warm mode without fields
+    assert L.mclbm_step(cav.handle, 1) == -3        # not initialised
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    assert L.mclbm_bind(cav.handle, small.data_ptr(), 1024, None) == -1
+    cav.init()
+    assert L.mclbm_fields(cav.handle, 0, cav.buffer.data_ptr()) == -1
+    assert L.mclbm_step(cav.handle, -1) == -1
+    cav.step(3)
+    assert cav.steps_done() == 3
+
+
+def test_determinism():
+    import torch
+    import paper_1511_04552_gb300 as m
+    outs = []
+    for _ in range(2):
+        cav = m.Cavity(96, 80, 1e5, 6.2, 0.03, 30e-9).init()
+        cav.step(300)
+        outs.append((cav.state_get(), cav.nusselt(), cav.mass(), cav.residual()))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
