@@ -32,6 +32,7 @@ UNIT = "MLUPS"
 BYTES_PER_LU = 216  # 27 FP32 populations read + 27 written per lattice-node update
 CHUNK = 1000        # time steps per benchmark step (one residual / Nusselt check interval)
 OUR_KERNELS_PER_REDUCTION = 5  # nusselt, residual + final, mass + final
+WORKLOADS = {"cavity256": workloads.CAVITY_256, "cavity1024": workloads.CAVITY_1024}
 
 
 def parse():
@@ -40,6 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity256", choices=sorted(WORKLOADS))
+    ap.add_argument("--chunk", type=int, default=CHUNK,
+                    help="time steps per benchmark step (default: one 1000-step check interval)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 1024^2 roofline case, the steady-Nu run and the CPU baseline")
     return ap.parse_args()
@@ -170,6 +174,26 @@ def cpu_baseline(seconds=10.0):
             "sample": "%d time steps of the %s cavity from rest (%.1f s)" % (n, w["name"], dt)}
 
 
+def ncu_traffic(workload_name):
+    """DRAM bytes per step launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1511_04552_gb300", "csrc", "mclbm_kernels.cu")
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != sha:
+            return None
+        return float(vals["%s_dram_bytes_per_launch" % workload_name.split("_")[0]])
+    except Exception:
+        return None
+
+
 def time_steps_only(cav, torch, nsteps):
     """Average duration of one step launch: events around back-to-back graph replays."""
     st = cav.stream
@@ -205,7 +229,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    w = workloads.CAVITY_256
+    w = WORKLOADS[args.workload]
+    CH = args.chunk
     nx, ny = w["nx"], w["ny"]
     cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
     cav.init()
@@ -215,7 +240,7 @@ def main():
     def bench_step(ev=None):
         if ev is not None:
             ev[0].record(st)
-        cav.step(CHUNK)
+        cav.step(CH)
         if ev is not None:
             ev[1].record(st)
         cav.nusselt()
@@ -240,12 +265,12 @@ def main():
         torch.cuda.synchronize()
     barrier()
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    step_time = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (args.steps * CHUNK)
+    step_time = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (args.steps * CH)
     if dist is not None:
         tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = float(tt.item())
-    lu = nx * ny * CHUNK * args.steps
+    lu = nx * ny * CH * args.steps
     value = lu * ws / elapsed / 1e6
     hbm_peak, peak_kind = peaks()
     achieved = BYTES_PER_LU * nx * ny / step_time / 1e9
@@ -256,17 +281,17 @@ def main():
     fields_host = torch.empty((8, ny, nx), dtype=torch.float32).pin_memory()
     e2e_cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
     for _ in range(max(1, args.warmup)):
-        e2e_cav.run_host(warm, CHUNK, 0xFF, fields_host)
+        e2e_cav.run_host(warm, CH, 0xFF, fields_host)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_cav.run_host(warm, CHUNK, 0xFF, fields_host)
+        e2e_cav.run_host(warm, CH, 0xFF, fields_host)
     e2e_time = time.perf_counter() - t0
     if dist is not None:
         tt = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_time = float(tt.item())
-    e2e_value = nx * ny * CHUNK * args.steps * ws / e2e_time / 1e6
+    e2e_value = nx * ny * CH * args.steps * ws / e2e_time / 1e6
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -279,19 +304,20 @@ def main():
         extras["hbm_case"] = {
             "workload": w4["name"], "mlups": w4["nx"] * w4["ny"] / t_big / 1e6,
             "roofline": {"bound": "hbm", "achieved": ach_big, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": ach_big / hbm_peak, "traffic": None,
+                         "frac": ach_big / hbm_peak, "traffic": ncu_traffic(w4["name"]),
                          "peak_kind": peak_kind, "bytes_per_launch": BYTES_PER_LU * w4["nx"] * w4["ny"],
                          "launch_us": t_big * 1e6}}
         del big
         torch.cuda.empty_cache()
         # cold start to steady Nu (1e-4 over two consecutive 1000-step checks)
-        sc = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"]).init()
+        w2 = workloads.CAVITY_256
+        sc = m.Cavity(w2["nx"], w2["ny"], w2["Ra"], w2["Pr"], w2["phi"], w2["d_p"]).init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = m.run_to_steady(sc, tol=1e-4, check_every=1000, consecutive=2, max_steps=400000)
         extras["steady_nu"] = {"wall_s": time.perf_counter() - t0, "steps": res["steps"],
                                "converged": res["converged"], "nu_hot": res["nu_hot"],
-                               "nu_cold": res["nu_cold"], "workload": w["name"]}
+                               "nu_cold": res["nu_cold"], "workload": w2["name"]}
         if ws == 1:
             extras["cpu_baseline"] = cpu_baseline()
 
@@ -302,18 +328,19 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w["name"], "nx": nx, "ny": ny, "Ra": w["Ra"], "Pr": w["Pr"],
-                       "phi": w["phi"], "d_p": w["d_p"], "time_steps_per_bench_step": CHUNK,
+                       "phi": w["phi"], "d_p": w["d_p"], "time_steps_per_bench_step": CH,
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "flushed between bench steps (256 MiB write); the 14 MB state is "
-                             "L2-resident within a bench step"},
+                       "l2": "flushed between bench steps (256 MiB write); state %.0f MB" % (
+                           2 * 27 * 4 * nx * ny / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm_peak, "traffic": ncu_traffic(w["name"]),
+                         "peak_kind": peak_kind,
                          "kernel": "step_kernel", "bytes_per_launch": BYTES_PER_LU * nx * ny,
                          "launch_us": step_time * 1e6},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * nx * ny * 4,
                     "d2h_bytes_per_step": 8 * nx * ny * 4 + 16},
-            "gpu_launches": args.steps * (CHUNK + OUR_KERNELS_PER_REDUCTION),
+            "gpu_launches": args.steps * (CH + OUR_KERNELS_PER_REDUCTION),
             "clocks": clk.summary(),
         }
         line.update(extras)
