@@ -38,6 +38,7 @@ extern "C" {
 #define MCLBM_ESTATE (-3)    /* call out of order (e.g. step before bind/init) */
 #define MCLBM_ECUDA (-4)     /* a CUDA runtime call failed; text in mclbm_last_error */
 #define MCLBM_EDIVERGED (-5) /* a reduction saw a non-finite value; sticky until mclbm_init */
+#define MCLBM_ETOOLARGE (-6) /* the lattice exceeds the fixed scratch of mclbm_mass_noalloc */
 
 /* ---- slip-mechanism switches (Eq 6 and Table 1; buoyancy of Eq 20) ----------------------- */
 #define MCLBM_F_BROWNIAN 1u
@@ -171,6 +172,26 @@ int mclbm_state_set(mclbm_t *h, const float *dev_in);
  * returns both Nusselt numbers (may be NULL). Syncs. */
 int mclbm_run_host(mclbm_t *h, const float *warm_host, int64_t n, uint32_t which,
                    float *fields_host, double *nu_hot, double *nu_cold);
+
+/* Component masses for callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is not allowed or not wanted, such as inside a stream capture, in a host
+ * application that hands out all device memory from its own fixed pool, or in a loop that
+ * must not pay for, or synchronise on, an allocation. Not a method of the paper (it has no
+ * counterpart there): the same FP64 sums as mclbm_mass, needing no handle and no buffer.
+ *   state_dev: caller-owned device array [27][ny][nx] FP32 in the layout of mclbm_state_get
+ *              (deviations from the rest state; only the 18 f planes are read).
+ *   rho_w0, rho_p0: the rest-state partial densities (mclbm_consts) added back per node.
+ *   mass_w, mass_p: host outputs. cuda_stream: the stream to run on (NULL: legacy default).
+ * Its scratch is a static device array of 2 x 8192 + 2 doubles (128 KiB) that every GPU which
+ * loads the library holds until the process exits: ny > 8192 or nx > 32768 returns
+ * MCLBM_ETOOLARGE. The first call on a device looks the array's device address up (with that
+ * device current), so make that first call before any stream capture. Calls that overlap on
+ * the GPU share the array and race: serialise them (one stream, or wait in between). Every
+ * scratch element a call reads is written earlier by the same call, so a previous call's
+ * contents never leak into a result. Calls no cudaMalloc or cudaFree. Syncs the stream.
+ * Returns MCLBM_OK, MCLBM_EINVAL, MCLBM_ETOOLARGE, MCLBM_ECUDA or MCLBM_EDIVERGED. */
+int mclbm_mass_noalloc(const float *state_dev, int nx, int ny, double rho_w0, double rho_p0,
+                       double *mass_w, double *mass_p, void *cuda_stream);
 
 /* Derived constants of the handle. */
 int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);

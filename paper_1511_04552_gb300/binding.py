@@ -11,7 +11,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmclbm.so")
 
-OK, EINVAL, EPARAM, ESTATE, ECUDA, EDIVERGED = 0, -1, -2, -3, -4, -5
+OK, EINVAL, EPARAM, ESTATE, ECUDA, EDIVERGED, ETOOLARGE = 0, -1, -2, -3, -4, -5, -6
 F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY = (
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127
@@ -25,7 +25,7 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
            "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
            "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
-           "mclbm_last_error", "mclbm_strerror")
+           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc")
 
 
 class Props(C.Structure):
@@ -96,6 +96,8 @@ def lib():
         L.mclbm_last_error.restype = C.c_char_p
         L.mclbm_strerror.argtypes = [C.c_int]
         L.mclbm_strerror.restype = C.c_char_p
+        L.mclbm_mass_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, vp]
+        L.mclbm_mass_noalloc.restype = C.c_int
         for name in ("mclbm_create", "mclbm_bind", "mclbm_init", "mclbm_step",
                      "mclbm_stream_only", "mclbm_fields", "mclbm_nusselt", "mclbm_mass",
                      "mclbm_residual", "mclbm_state_get", "mclbm_state_set", "mclbm_run_host",
