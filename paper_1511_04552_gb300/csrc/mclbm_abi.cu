@@ -122,7 +122,7 @@ int build_graph(mclbm_t* h, int from) {
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
-    le = launch_step(step_args(h, (from + s) & 1), h->cfg.bx, h->cap_stream);
+    le = launch_step(step_args(h, (from + s) & 1), h->cfg, h->cap_stream);
   cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -280,7 +280,7 @@ int mclbm_step(mclbm_t* h, int64_t n) {
     h->steps += kGraphSteps;
   }
   for (; left > 0; --left) {
-    CK(h, launch_step(step_args(h, h->cur), h->cfg.bx, h->stream));
+    CK(h, launch_step(step_args(h, h->cur), h->cfg, h->stream));
     h->cur ^= 1;
     h->steps += 1;
   }

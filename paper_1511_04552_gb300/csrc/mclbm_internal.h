@@ -64,11 +64,12 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
-  int bx;    // columns per CTA (32, 64 or 128)
-  int rows;  // rows per CTA strip
+  int variant;  // 0: tile kernel (one node per thread); 1: row-marching kernel
+  int bx;       // row-marching kernel: columns per CTA (32, 64 or 128)
+  int rows;     // row-marching kernel: rows per CTA strip
 };
 StepConfig choose_step_config(int nx, int ny);
-cudaError_t launch_step(const StepArgs& a, int bx, cudaStream_t st);
+cudaError_t launch_step(const StepArgs& a, const StepConfig& c, cudaStream_t st);
 cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
                                cudaStream_t st);
 cudaError_t launch_init(float* dst, const Layout& L, const StepConsts& k, const float* warm,

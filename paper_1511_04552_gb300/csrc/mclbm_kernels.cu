@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 
 #include "mclbm_internal.h"
 
@@ -347,6 +349,73 @@ __global__ void __launch_bounds__(BX + 32) step_kernel(const StepArgs a) {
   }
 }
 
+// ---- the fused step, tile variant --------------------------------------------------------------
+// One node per thread on a TX x TY tile. Every thread pulls its node's 27 populations; the
+// first 2 TX + 2 TY threads also pull the 18 f^p and g populations of one node of the ring
+// around the tile, all in the same load phase, so each CTA has all its loads in flight at once
+// and the next CTA on the SM overlaps its compute. theta' and rho'^p of the tile and ring go to
+// shared memory; one barrier; then every thread finishes its node.
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 2) step_tile_kernel(const StepArgs a) {
+  constexpr int NRING = 2 * TX + 2 * TY;
+  static_assert(NRING <= TX * TY, "at most one ring node per thread");
+  __shared__ float s_th[TY + 2][TX + 2];
+  __shared__ float s_rp[TY + 2][TX + 2];
+  const Layout L = a.L;
+  const float* __restrict__ src = a.src;
+  const int t = threadIdx.x;
+  const int tx = t % TX, ty = t / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < L.nx && j < L.ny;
+
+  // this thread's ring node, tile coordinates in [-1, TX] x [-1, TY] without the corners
+  int hx = 0, hy = 0;
+  bool ring = false;
+  if (t < NRING) {
+    if (t < TX) {
+      hx = t;
+      hy = -1;
+    } else if (t < 2 * TX) {
+      hx = t - TX;
+      hy = TY;
+    } else if (t < 2 * TX + TY) {
+      hx = -1;
+      hy = t - 2 * TX;
+    } else {
+      hx = TX;
+      hy = t - 2 * TX - TY;
+    }
+    const int gi = i0 + hx, gj = j0 + hy;
+    ring = gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
+  }
+  float fw[kQ], fp[kQ], g[kQ];
+  float hw[kQ], hp[kQ], hg[kQ];
+  if (active) pull_node<true>(src, L, i, j, fw, fp, g, a.k.inv_nx);
+  if (ring) pull_node<false>(src, L, i0 + hx, j0 + hy, hw, hp, hg, a.k.inv_nx);
+  if (active) {
+    s_th[ty + 1][tx + 1] = sum9(g);
+    s_rp[ty + 1][tx + 1] = sum9(fp);
+  }
+  if (ring) {
+    s_th[hy + 1][hx + 1] = sum9(hg);
+    s_rp[hy + 1][hx + 1] = sum9(hp);
+  }
+  __syncthreads();
+  if (!active) return;
+  const float th = s_th[ty + 1][tx + 1], rp = s_rp[ty + 1][tx + 1];
+  // theta deviations: the isothermal ghost 2 T_wall - theta is -theta' in deviation form
+  const float thW = (i > 0) ? s_th[ty + 1][tx] : -th;
+  const float thE = (i + 1 < L.nx) ? s_th[ty + 1][tx + 2] : -th;
+  const float thS = (j > 0) ? s_th[ty][tx + 1] : th;
+  const float thN = (j + 1 < L.ny) ? s_th[ty + 2][tx + 1] : th;
+  const float rpW = (i > 0) ? s_rp[ty + 1][tx] : rp;
+  const float rpE = (i + 1 < L.nx) ? s_rp[ty + 1][tx + 2] : rp;
+  const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
+  const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
+  collide_store(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+}
+
 // ---- streaming only (test hook) -------------------------------------------------------------
 __global__ void stream_only_kernel(const float* __restrict__ src, float* __restrict__ dst,
                                    const Layout L, float s) {
@@ -572,6 +641,9 @@ int grid_for(int64_t n, int block, int cap) {
 
 StepConfig choose_step_config(int nx, int ny) {
   StepConfig c;
+  // MCLBM_STEP_VARIANT=march selects the row-marching kernel (kept for comparison)
+  const char* v = std::getenv("MCLBM_STEP_VARIANT");
+  c.variant = (v && std::strcmp(v, "march") == 0) ? 1 : 0;
   c.bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
   const int tiles_x = (nx + c.bx - 1) / c.bx;
   // aim for at least ~2 CTAs per SM on 152 SMs, with strips of 4 to 32 rows
@@ -581,9 +653,15 @@ StepConfig choose_step_config(int nx, int ny) {
   return c;
 }
 
-cudaError_t launch_step(const StepArgs& a, int bx, cudaStream_t st) {
-  dim3 grid((a.L.nx + bx - 1) / bx, (a.L.ny + a.rows - 1) / a.rows);
-  switch (bx) {
+cudaError_t launch_step(const StepArgs& a, const StepConfig& c, cudaStream_t st) {
+  if (c.variant == 0) {
+    constexpr int TX = 32, TY = 8;
+    dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
+    step_tile_kernel<TX, TY><<<grid, TX * TY, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  dim3 grid((a.L.nx + c.bx - 1) / c.bx, (a.L.ny + a.rows - 1) / a.rows);
+  switch (c.bx) {
     case 32:
       step_kernel<32><<<grid, 32 + 32, 0, st>>>(a);
       break;
