@@ -39,6 +39,8 @@ extern "C" {
 #define MCLBM_ECUDA (-4)     /* a CUDA runtime call failed; text in mclbm_last_error */
 #define MCLBM_EDIVERGED (-5) /* a reduction saw a non-finite value; sticky until mclbm_init */
 #define MCLBM_ETOOLARGE (-6) /* the lattice exceeds the fixed scratch of mclbm_mass_noalloc */
+#define MCLBM_ETIMEOUT (-7)  /* a step kernel gave up a bounded device wait (2 s); the state is
+                                not valid; reported by the next reduction, cleared by init */
 
 /* ---- slip-mechanism switches (Eq 6 and Table 1; buoyancy of Eq 20) ----------------------- */
 #define MCLBM_F_BROWNIAN 1u
@@ -131,7 +133,9 @@ int mclbm_bind(mclbm_t *h, void *dev_buf, size_t bytes, void *cuda_stream);
 int mclbm_init(mclbm_t *h, int mode, const float *warm_dev);
 
 /* Advances n >= 0 time steps (Eqs 18-19 with the forces of Table 1 and the walls of
- * Eqs 34-36), in captured CUDA graphs of 64 steps plus single launches. Async. */
+ * Eqs 34-36), in captured CUDA graphs of 64 steps plus single launches. Async. A step kernel
+ * that gives up a bounded wait on its own data movement sets an error word instead of
+ * hanging; the next mclbm_nusselt, mclbm_mass or mclbm_residual returns MCLBM_ETIMEOUT. */
 int mclbm_step(mclbm_t *h, int64_t n);
 
 /* Advances one time step of streaming only (no collision, no forces): a test hook for the

@@ -11,7 +11,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmclbm.so")
 
-OK, EINVAL, EPARAM, ESTATE, ECUDA, EDIVERGED, ETOOLARGE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, EPARAM, ESTATE, ECUDA, EDIVERGED, ETOOLARGE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY = (
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127

@@ -30,6 +30,8 @@ struct mclbm {
   float* staging = nullptr;  // [8][ny][nx]
   double* partials = nullptr;
   double* red = nullptr;
+  int* err_dev = nullptr;  // device error word of the step kernels (bounded waits)
+  CUtensorMap tmap;        // two-level state for the TMA step kernel
   int cur = 0;
   bool initialised = false;
   bool diverged = false;
@@ -65,7 +67,7 @@ int cuda_fail(mclbm_t* h, cudaError_t e, const char* where) {
   } while (0)
 
 struct Regions {
-  size_t state, snap, staging, partials, red, total;
+  size_t state, snap, staging, partials, red, err, total;
 };
 
 Regions regions(const mclbm_t* h) {
@@ -82,6 +84,8 @@ Regions regions(const mclbm_t* h) {
   off += align_up((size_t)kMaxRedBlocks * kRedWidth * sizeof(double), 256);
   r.red = off;
   off += align_up((size_t)kRedWidth * sizeof(double), 256);
+  r.err = off;
+  off += 256;
   r.total = off;
   return r;
 }
@@ -111,6 +115,8 @@ StepArgs step_args(const mclbm_t* h, int from) {
   a.dst = h->state[1 - from];
   a.L = h->L;
   a.rows = h->cfg.rows;
+  a.z_src = from * kPlanes;
+  a.err = h->err_dev;
   a.k = h->k;
   return a;
 }
@@ -122,7 +128,7 @@ int build_graph(mclbm_t* h, int from) {
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
-    le = launch_step(step_args(h, (from + s) & 1), h->cfg, h->cap_stream);
+    le = launch_step(step_args(h, (from + s) & 1), h->cfg, &h->tmap, h->cap_stream);
   cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -138,9 +144,15 @@ int build_graph(mclbm_t* h, int from) {
   return MCLBM_OK;
 }
 
+// Copies a reduction result to the host and waits; also reports a step kernel that gave up
+// a bounded wait since the last init.
 int d2h_sync(mclbm_t* h, void* host, const void* dev, size_t bytes) {
+  int err = 0;
   CK(h, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(&err, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  if (err) return fail(h, MCLBM_ETIMEOUT, "a step kernel gave up a bounded wait (error word %d)",
+                       err);
   return MCLBM_OK;
 }
 
@@ -241,6 +253,18 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->staging = reinterpret_cast<float*>(h->buf + r.staging);
   h->partials = reinterpret_cast<double*>(h->buf + r.partials);
   h->red = reinterpret_cast<double*>(h->buf + r.red);
+  h->err_dev = reinterpret_cast<int*>(h->buf + r.err);
+  // device-dependent set-up of the step kernel; the TMA variant falls back to the plain tile
+  // kernel if the device cannot run it
+  h->cfg = choose_step_config(h->nx, h->ny);
+  if (h->cfg.variant == 2) {
+    if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
+        make_state_tensor_map(&h->tmap, h->state[0], h->L, h->cfg.tma_ty) != cudaSuccess) {
+      cudaGetLastError();
+      h->cfg.variant = 0;
+    }
+  }
+  CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
   h->cur = 0;
   h->initialised = false;
   h->diverged = false;
@@ -257,6 +281,7 @@ int mclbm_init(mclbm_t* h, int mode, const float* warm_dev) {
   if (mode == MCLBM_INIT_WARM && !warm_dev)
     return fail(h, MCLBM_EINVAL, "MCLBM_INIT_WARM needs warm fields");
   h->cur = 0;
+  CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
   CK(h, launch_init(h->state[0], h->L, h->k, mode == MCLBM_INIT_WARM ? warm_dev : nullptr,
                     h->stream));
   h->steps = 0;
@@ -280,7 +305,7 @@ int mclbm_step(mclbm_t* h, int64_t n) {
     h->steps += kGraphSteps;
   }
   for (; left > 0; --left) {
-    CK(h, launch_step(step_args(h, h->cur), h->cfg, h->stream));
+    CK(h, launch_step(step_args(h, h->cur), h->cfg, &h->tmap, h->stream));
     h->cur ^= 1;
     h->steps += 1;
   }
@@ -382,6 +407,7 @@ int mclbm_state_set(mclbm_t* h, const float* dev_in) {
   if (rc) return rc;
   if (!dev_in) return fail(h, MCLBM_EINVAL, "NULL input");
   h->cur = 0;
+  CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
   CK(h, launch_state_copy(dev_in, h->state[0], h->L, false, h->stream));
   h->steps = 0;
   h->initialised = true;
@@ -443,6 +469,8 @@ const char* mclbm_strerror(int code) {
     case MCLBM_ESTATE: return "MCLBM_ESTATE";
     case MCLBM_ECUDA: return "MCLBM_ECUDA";
     case MCLBM_EDIVERGED: return "MCLBM_EDIVERGED";
+    case MCLBM_ETOOLARGE: return "MCLBM_ETOOLARGE";
+    case MCLBM_ETIMEOUT: return "MCLBM_ETIMEOUT";
     default: return "unknown";
   }
 }

@@ -1,6 +1,7 @@
 // Internal declarations of libmclbm (GB300 / sm_103a). Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -51,7 +52,9 @@ struct StepArgs {
   const float* src;
   float* dst;
   Layout L;
-  int rows;  // rows per CTA strip
+  int rows;   // row-marching kernel: rows per CTA strip
+  int z_src;  // TMA kernel: first plane of the source level in the two-level tensor (0 or 27)
+  int* err;   // device error word: bit 0 set when a bounded wait gave up
   StepConsts k;
 };
 
@@ -64,12 +67,20 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
-  int variant;  // 0: tile kernel (one node per thread); 1: row-marching kernel
+  int variant;  // 0: tile kernel; 1: row-marching kernel; 2: TMA-staged persistent tiles
   int bx;       // row-marching kernel: columns per CTA (32, 64 or 128)
   int rows;     // row-marching kernel: rows per CTA strip
+  int tma_ty;   // TMA kernel: tile height (8 or 16; the tile is 32 wide)
+  int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
 };
 StepConfig choose_step_config(int nx, int ny);
-cudaError_t launch_step(const StepArgs& a, const StepConfig& c, cudaStream_t st);
+// Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
+// may fall back to variant 0. Needs the device current.
+cudaError_t prepare_step(StepConfig* c, const Layout& L);
+// Tensor map of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernel.
+cudaError_t make_state_tensor_map(CUtensorMap* map, float* state0, const Layout& L, int tile_ty);
+cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                        cudaStream_t st);
 cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
                                cudaStream_t st);
 cudaError_t launch_init(float* dst, const Layout& L, const StepConsts& k, const float* warm,

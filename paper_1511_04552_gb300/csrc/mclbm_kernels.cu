@@ -15,6 +15,8 @@
 // 4-row ring in shared memory, so the gradients at row j see rows j-1, j, j+1 at the same
 // time level. The strip's halo rows and columns are pulled (18 planes) only for their moments.
 // No tensor cores: this is a memory-bound stencil.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -416,6 +418,219 @@ __global__ void __launch_bounds__(TX * TY, 2) step_tile_kernel(const StepArgs a)
   collide_store(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
 }
 
+// ---- the fused step, TMA-staged persistent variant -------------------------------------------
+// Each persistent CTA walks tiles of 32 x TY nodes. For every tile one TMA tensor load brings
+// the tile's window of all 27 planes (columns i0-4 .. i0+35, rows j0-2 .. j0+TY+1; the domain
+// outside reads as zeros and is never used) into shared memory, double-buffered: while a tile
+// is computed from one buffer the next tile's window streams into the other, so the HBM stays
+// busy without the compute warps waiting on their own loads. Completion is tracked by one
+// mbarrier per buffer; every wait on it is bounded (2 s on %globaltimer), after which the
+// kernel sets bit 0 of the error word, drains its copies (bounded) and returns.
+namespace tma {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase with the given parity to complete; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t k = 0; k < (1u << 26); ++k) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                        uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+}  // namespace tma
+
+constexpr int kTmaTX = 32;               // tile width
+constexpr int kTmaWX = kTmaTX + 8;       // window width: 4 columns each side (16-byte aligned x)
+template <int TY>
+struct TmaTile {
+  static constexpr int WY = TY + 4;      // window height: 2 rows each side
+  static constexpr int WPLANE = kTmaWX * WY;
+  static constexpr uint32_t BYTES = (uint32_t)kPlanes * WPLANE * 4u;
+  static constexpr size_t SMEM = 2 * (size_t)BYTES;  // dynamic shared memory: two windows
+};
+
+// Pull of node (i, j) from a window whose element (wx, wy) of plane p is
+// w[p * WPLANE + wy * kTmaWX + wx]; (wx, wy) is the node's own position in the window.
+template <bool FULL, int WPLANE>
+__device__ __forceinline__ void pull_window(const float* w, const Layout& L, int i, int j, int wx,
+                                            int wy, float* fw, float* fp, float* g, float s) {
+  const int self = wy * kTmaWX + wx;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int si = i - ex(q), sj = j - ey(q);
+    const bool inx = (unsigned)si < (unsigned)L.nx;
+    const bool iny = (unsigned)sj < (unsigned)L.ny;
+    const int src = self - ey(q) * kTmaWX - ex(q);
+    if (inx && iny) {
+      if (FULL) fw[q] = w[q * WPLANE + src];
+      fp[q] = w[(kQ + q) * WPLANE + src];
+      g[q] = w[(2 * kQ + q) * WPLANE + src];
+    } else {
+      if (FULL) fw[q] = w[opp(q) * WPLANE + self];
+      fp[q] = w[(kQ + opp(q)) * WPLANE + self];
+      if (!inx)
+        g[q] = -w[(2 * kQ + opp(q)) * WPLANE + self];
+      else
+        g[q] = w[(2 * kQ + mir(q)) * WPLANE + self - ex(q)];
+    }
+    if (ex(q) != 0) g[q] += (float)ex(q) * wq(q) * s;
+  }
+}
+
+template <int TY>
+__global__ void __launch_bounds__(kTmaTX * TY, (TY <= 8 ? 2 : 1))
+    step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+  constexpr int TX = kTmaTX;
+  constexpr int NRING = 2 * TX + 2 * TY;
+  constexpr int WPLANE = TmaTile<TY>::WPLANE;
+  constexpr uint32_t BYTES = TmaTile<TY>::BYTES;
+  static_assert(NRING <= TX * TY, "at most one ring node per thread");
+  static_assert(BYTES % 128 == 0, "second window stays 128-byte aligned");
+  extern __shared__ __align__(128) float win_smem[];
+  __shared__ float s_th[TY + 2][TX + 2];
+  __shared__ float s_rp[TY + 2][TX + 2];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_abort;
+
+  const Layout L = a.L;
+  const int t = threadIdx.x;
+  const int tx = t % TX, ty = t / TX;
+  const int tiles_x = (L.nx + TX - 1) / TX;
+  const int n_tiles = tiles_x * ((L.ny + TY - 1) / TY);
+  const uint32_t bar0 = tma::smem_u32(&bars[0]);
+  const uint32_t win0 = tma::smem_u32(win_smem);
+
+  if (t == 0) {
+    tma::mbar_init(bar0, 1);
+    tma::mbar_init(bar0 + 8, 1);
+    tma::fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  // this thread's ring node (tile coordinates, corners excluded)
+  int hx = 0, hy = 0;
+  if (t < NRING) {
+    if (t < TX) {
+      hx = t;
+      hy = -1;
+    } else if (t < 2 * TX) {
+      hx = t - TX;
+      hy = TY;
+    } else if (t < 2 * TX + TY) {
+      hx = -1;
+      hy = t - 2 * TX;
+    } else {
+      hx = TX;
+      hy = t - 2 * TX - TY;
+    }
+  }
+
+  int tile = blockIdx.x;
+  if (t == 0 && tile < n_tiles) {
+    tma::mbar_expect_tx(bar0, BYTES);
+    tma::load_3d(win0, &tmap, (tile % tiles_x) * TX - 4, (tile / tiles_x) * TY - 2, a.z_src, bar0);
+  }
+  for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
+    const int stage = it & 1;
+    const int next = tile + gridDim.x;
+    if (t == 0 && next < n_tiles) {
+      // the other window was last read in the previous iteration, which ended in a barrier
+      tma::fence_proxy_async();
+      const uint32_t bar = bar0 + 8u * (stage ^ 1);
+      tma::mbar_expect_tx(bar, BYTES);
+      tma::load_3d(win0 + (stage ^ 1) * BYTES, &tmap, (next % tiles_x) * TX - 4,
+                   (next / tiles_x) * TY - 2, a.z_src, bar);
+    }
+    const bool ok = tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
+    const float* w = win_smem + stage * (BYTES / 4);
+    const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < L.nx && j < L.ny;
+    const int gi = i0 + hx, gj = j0 + hy;
+    const bool ring = t < NRING && gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
+    float fw[kQ], fp[kQ], g[kQ];
+    if (active) {
+      pull_window<true, WPLANE>(w, L, i, j, tx + 4, ty + 2, fw, fp, g, a.k.inv_nx);
+      s_th[ty + 1][tx + 1] = sum9(g);
+      s_rp[ty + 1][tx + 1] = sum9(fp);
+    }
+    if (ring) {
+      float hw[kQ], hp[kQ], hg[kQ];
+      pull_window<false, WPLANE>(w, L, gi, gj, hx + 4, hy + 2, hw, hp, hg, a.k.inv_nx);
+      s_th[hy + 1][hx + 1] = sum9(hg);
+      s_rp[hy + 1][hx + 1] = sum9(hp);
+    }
+    if (!ok) s_abort = 1;
+    __syncthreads();
+    if (s_abort) {
+      if (t == 0) {
+        atomicOr(a.err, 1);
+        // drain: this tile's copy and, if issued, the next one (bounded waits)
+        tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
+        if (next < n_tiles) tma::mbar_wait(bar0 + 8u * (stage ^ 1), ((it + 1) >> 1) & 1);
+      }
+      return;
+    }
+    if (active) {
+      const float th = s_th[ty + 1][tx + 1], rp = s_rp[ty + 1][tx + 1];
+      // theta deviations: the isothermal ghost 2 T_wall - theta is -theta' in deviation form
+      const float thW = (i > 0) ? s_th[ty + 1][tx] : -th;
+      const float thE = (i + 1 < L.nx) ? s_th[ty + 1][tx + 2] : -th;
+      const float thS = (j > 0) ? s_th[ty][tx + 1] : th;
+      const float thN = (j + 1 < L.ny) ? s_th[ty + 2][tx + 1] : th;
+      const float rpW = (i > 0) ? s_rp[ty + 1][tx] : rp;
+      const float rpE = (i + 1 < L.nx) ? s_rp[ty + 1][tx + 2] : rp;
+      const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
+      const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
+      collide_store(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+    }
+    __syncthreads();  // the window and the moment tile are free again
+  }
+}
+
 // ---- streaming only (test hook) -------------------------------------------------------------
 __global__ void stream_only_kernel(const float* __restrict__ src, float* __restrict__ dst,
                                    const Layout L, float s) {
@@ -641,9 +856,16 @@ int grid_for(int64_t n, int block, int cap) {
 
 StepConfig choose_step_config(int nx, int ny) {
   StepConfig c;
-  // MCLBM_STEP_VARIANT=march selects the row-marching kernel (kept for comparison)
+  // default: TMA-staged tiles for lattices with a few tiles per SM, the plain tile kernel below.
+  // MCLBM_STEP_VARIANT = tile | march | tma overrides (diagnostics and comparisons).
+  c.variant = (nx >= 64 && ny >= 32) ? 2 : 0;
   const char* v = std::getenv("MCLBM_STEP_VARIANT");
-  c.variant = (v && std::strcmp(v, "march") == 0) ? 1 : 0;
+  if (v && std::strcmp(v, "tile") == 0) c.variant = 0;
+  if (v && std::strcmp(v, "march") == 0) c.variant = 1;
+  if (v && std::strcmp(v, "tma") == 0) c.variant = 2;
+  const char* ty = std::getenv("MCLBM_TMA_TILE_Y");
+  c.tma_ty = (ty && std::strcmp(ty, "16") == 0) ? 16 : 8;
+  c.grid = 0;
   c.bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
   const int tiles_x = (nx + c.bx - 1) / c.bx;
   // aim for at least ~2 CTAs per SM on 152 SMs, with strips of 4 to 32 rows
@@ -653,7 +875,63 @@ StepConfig choose_step_config(int nx, int ny) {
   return c;
 }
 
-cudaError_t launch_step(const StepArgs& a, const StepConfig& c, cudaStream_t st) {
+namespace {
+template <int TY>
+cudaError_t prepare_tma(StepConfig* c, const Layout& L) {
+  const size_t smem = TmaTile<TY>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<TY>, kTmaTX * TY,
+                                                    smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int tiles = ((L.nx + kTmaTX - 1) / kTmaTX) * ((L.ny + TY - 1) / TY);
+  c->grid = tiles < per_sm * sms ? tiles : per_sm * sms;
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t prepare_step(StepConfig* c, const Layout& L) {
+  if (c->variant != 2) return cudaSuccess;
+  return c->tma_ty == 16 ? prepare_tma<16>(c, L) : prepare_tma<8>(c, L);
+}
+
+cudaError_t make_state_tensor_map(CUtensorMap* map, float* state0, const Layout& L, int tile_ty) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)(2 * kPlanes)};
+  const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4u, (cuuint64_t)L.plane * 4u};
+  const cuuint32_t box[3] = {(cuuint32_t)kTmaWX, (cuuint32_t)(tile_ty + 4), (cuuint32_t)kPlanes};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, state0, dims, strides, box, elem,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                        cudaStream_t st) {
+  if (c.variant == 2) {
+    if (!map || c.grid < 1) return cudaErrorInvalidValue;
+    if (c.tma_ty == 16)
+      step_tma_kernel<16><<<c.grid, kTmaTX * 16, TmaTile<16>::SMEM, st>>>(*map, a);
+    else
+      step_tma_kernel<8><<<c.grid, kTmaTX * 8, TmaTile<8>::SMEM, st>>>(*map, a);
+    return cudaGetLastError();
+  }
   if (c.variant == 0) {
     constexpr int TX = 32, TY = 8;
     dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
