@@ -114,7 +114,6 @@ StepArgs step_args(const mclbm_t* h, int from) {
   a.src = h->state[from];
   a.dst = h->state[1 - from];
   a.L = h->L;
-  a.rows = h->cfg.rows;
   a.z_src = from * kPlanes;
   a.err = h->err_dev;
   a.k = h->k;

@@ -52,7 +52,6 @@ struct StepArgs {
   const float* src;
   float* dst;
   Layout L;
-  int rows;   // row-marching kernel: rows per CTA strip
   int z_src;  // TMA kernel: first plane of the source level in the two-level tensor (0 or 27)
   int* err;   // device error word: bit 0 set when a bounded wait gave up
   StepConsts k;
@@ -67,9 +66,7 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
-  int variant;  // 0: tile kernel; 1: row-marching kernel; 2: TMA-staged persistent tiles
-  int bx;       // row-marching kernel: columns per CTA (32, 64 or 128)
-  int rows;     // row-marching kernel: rows per CTA strip
+  int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles
   int tma_ty;   // TMA kernel: tile height (8 or 16; the tile is 32 wide)
   int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
 };

@@ -9,11 +9,10 @@
 // The step is one fused kernel (one launch per time step): pull streaming with the wall rules
 // (Eqs 18-19 LHS, 34-36), moments (Eqs 29-32), same-time-level gradients of theta and phi,
 // the slip forces of Table 1 (Eqs 4, 6, 20), the exact drag impulse, BGK collision with
-// forcing (Eqs 18-19 RHS, 26-28, 24) and the store. A CTA owns a strip of BX columns and
-// `rows` rows and marches up it: each thread keeps its column's current row of 27 pulled
-// populations in registers while it pulls the next row, whose theta and rho^p go to a
-// 4-row ring in shared memory, so the gradients at row j see rows j-1, j, j+1 at the same
-// time level. The strip's halo rows and columns are pulled (18 planes) only for their moments.
+// forcing (Eqs 18-19 RHS, 26-28, 24) and the store. Same-time-level gradients need theta and
+// rho^p of the neighbours after streaming: a CTA pulls its tile and the ring of nodes around
+// it, puts their moments in shared memory, and then finishes its own nodes. Two variants:
+// the TMA-staged persistent kernel (default) and a plain tile kernel for small lattices.
 // No tensor cores: this is a memory-bound stencil.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -251,122 +250,43 @@ __device__ __forceinline__ void collide_store(const StepConsts& k, const Layout&
   }
 
   // BGK collision with forcing 3 W_q e_q.F on the common velocity (Eqs 18, 26), in deviation
-  // form: f' <- f' + (W_q rho' + rho P_q - f') / tau + A_q e_q.F; g likewise with theta.
+  // form: f' <- (1 - 1/tau) f' + (W_q rho' + rho P_q) / tau + A_q e_q.F; g likewise with theta.
+  // Opposite directions share the even part of P_q (B (e.u)^2 - C u.u) and negate the odd part
+  // (A e.u) and the forcing, so the loop runs over the four pairs (q, -q).
   const float tau_t = Yw * k.tau_tw + Yp * k.tau_tp;  // Eq 24 with local mass fractions
-  const float inv_tau_t = 1.0f / tau_t;
+  const float om_t = 1.0f / tau_t;
+  const float om_w = k.inv_tau_w, om_p = k.inv_tau_p;
+  const float keep_w = 1.0f - om_w, keep_p = 1.0f - om_p, keep_t = 1.0f - om_t;
   const float usq = ux * ux + uy * uy;
   const size_t o = (size_t)j * L.pitch + i;
-  float sw = 0.0f, sp = 0.0f, sg = 0.0f;
+  float sw = 0.0f, sp = 0.0f, sg = 0.0f;  // half the sum of the moving equilibria
 #pragma unroll
-  for (int q = 1; q < kQ; ++q) {
+  for (int pr = 0; pr < 4; ++pr) {
+    const int q = pr == 0 ? 1 : (pr == 1 ? 2 : (pr == 2 ? 5 : 6));
+    const int qo = opp(q);
     const float eu = (float)ex(q) * ux + (float)ey(q) * uy;
-    const float P = eu * (aq(q) + bq(q) * eu) - cq(q) * usq;
+    const float even = bq(q) * eu * eu - cq(q) * usq;
+    const float odd = aq(q) * eu;
     const float W = wq(q);
-    const float eqw = W * m.rw + rw * P;
-    const float eqp = W * m.rp + rp * P;
-    const float eqg = W * m.th + th * P;
-    sw += eqw;
-    sp += eqp;
-    sg += eqg;
+    const float tw = W * m.rw + rw * even, dw = rw * odd;
+    const float tp = W * m.rp + rp * even, dp = rp * odd;
+    const float tg = W * m.th + th * even, dg = th * odd;
+    sw += tw;
+    sp += tp;
+    sg += tg;
     const float Sw = aq(q) * ((float)ex(q) * Fwx + (float)ey(q) * Fwy);
     const float Sp = aq(q) * ((float)ex(q) * Fpx + (float)ey(q) * Fpy);
-    dst[(size_t)q * L.plane + o] = fw[q] + (eqw - fw[q]) * k.inv_tau_w + Sw;
-    dst[(size_t)(kQ + q) * L.plane + o] = fp[q] + (eqp - fp[q]) * k.inv_tau_p + Sp;
-    dst[(size_t)(2 * kQ + q) * L.plane + o] = g[q] + (eqg - g[q]) * inv_tau_t;
+    dst[(size_t)q * L.plane + o] = fmaf(fw[q], keep_w, fmaf(om_w, tw + dw, Sw));
+    dst[(size_t)qo * L.plane + o] = fmaf(fw[qo], keep_w, fmaf(om_w, tw - dw, -Sw));
+    dst[(size_t)(kQ + q) * L.plane + o] = fmaf(fp[q], keep_p, fmaf(om_p, tp + dp, Sp));
+    dst[(size_t)(kQ + qo) * L.plane + o] = fmaf(fp[qo], keep_p, fmaf(om_p, tp - dp, -Sp));
+    dst[(size_t)(2 * kQ + q) * L.plane + o] = fmaf(g[q], keep_t, om_t * (tg + dg));
+    dst[(size_t)(2 * kQ + qo) * L.plane + o] = fmaf(g[qo], keep_t, om_t * (tg - dg));
   }
   // rest populations: equilibrium = zeroth moment minus the moving equilibria
-  dst[o] = fw[0] + ((m.rw - sw) - fw[0]) * k.inv_tau_w;
-  dst[(size_t)kQ * L.plane + o] = fp[0] + ((m.rp - sp) - fp[0]) * k.inv_tau_p;
-  dst[(size_t)(2 * kQ) * L.plane + o] = g[0] + ((m.th - sg) - g[0]) * inv_tau_t;
-}
-
-// ---- the fused step ------------------------------------------------------------------------
-template <int BX>
-__global__ void __launch_bounds__(BX + 32) step_kernel(const StepArgs a) {
-  __shared__ float s_th[4][BX + 2];
-  __shared__ float s_rp[4][BX + 2];
-  const Layout L = a.L;
-  const float* __restrict__ src = a.src;
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * BX;
-  const int j0 = blockIdx.y * a.rows;
-  const int j1 = min(j0 + a.rows, L.ny);
-
-  // Role of the thread: an interior column (tid < BX) or one of the two halo columns.
-  int col = -1, sidx = 0;
-  bool interior = false;
-  if (tid < BX) {
-    col = i0 + tid;
-    sidx = tid + 1;
-    interior = true;
-  } else if (tid == BX) {
-    col = i0 - 1;
-    sidx = 0;
-  } else if (tid == BX + 1) {
-    col = i0 + BX;
-    sidx = BX + 1;
-  }
-  const bool active = col >= 0 && col < L.nx;
-
-  float fwa[kQ], fpa[kQ], ga[kQ];  // row j
-  float fwb[kQ], fpb[kQ], gb[kQ];  // row j + 1
-
-  // moments of a halo row (f^p, g only) into the ring
-  auto halo_row = [&](int r) {
-    if (active) {
-      float tw[kQ], tp[kQ], tg[kQ];
-      pull_node<false>(src, L, col, r, tw, tp, tg, a.k.inv_nx);
-      s_th[r & 3][sidx] = sum9(tg);
-      s_rp[r & 3][sidx] = sum9(tp);
-    }
-  };
-  // full pull of row r for interior threads, halo moments for halo threads
-  auto load_row = [&](int r, float* fw, float* fp, float* g) {
-    if (active) {
-      if (interior) {
-        pull_node<true>(src, L, col, r, fw, fp, g, a.k.inv_nx);
-        s_th[r & 3][sidx] = sum9(g);
-        s_rp[r & 3][sidx] = sum9(fp);
-      } else {
-        float tw[kQ];
-        pull_node<false>(src, L, col, r, tw, fp, g, a.k.inv_nx);
-        s_th[r & 3][sidx] = sum9(g);
-        s_rp[r & 3][sidx] = sum9(fp);
-      }
-    }
-  };
-  // row j: pull row j+1 into (nw, np_, ng), then finish row j from (cw, cp, cg)
-  auto body = [&](int j, const float* cw, const float* cp, const float* cg, float* nw, float* np_,
-                  float* ng) {
-    if (j + 1 < L.ny) {
-      if (j + 1 < j1)
-        load_row(j + 1, nw, np_, ng);
-      else
-        halo_row(j + 1);
-    }
-    __syncthreads();
-    if (interior && active) {
-      const int s = sidx;
-      const float th = s_th[j & 3][s], rp = s_rp[j & 3][s];
-      // theta deviations: the isothermal ghost 2 T_wall - theta is -theta' in deviation form
-      const float thW = (col > 0) ? s_th[j & 3][s - 1] : -th;
-      const float thE = (col + 1 < L.nx) ? s_th[j & 3][s + 1] : -th;
-      const float rpW = (col > 0) ? s_rp[j & 3][s - 1] : rp;
-      const float rpE = (col + 1 < L.nx) ? s_rp[j & 3][s + 1] : rp;
-      const float thS = (j > 0) ? s_th[(j - 1) & 3][s] : th;
-      const float rpS = (j > 0) ? s_rp[(j - 1) & 3][s] : rp;
-      const float thN = (j + 1 < L.ny) ? s_th[(j + 1) & 3][s] : th;
-      const float rpN = (j + 1 < L.ny) ? s_rp[(j + 1) & 3][s] : rp;
-      collide_store(a.k, L, a.dst, col, j, cw, cp, cg, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
-    }
-  };
-
-  if (j0 > 0) halo_row(j0 - 1);
-  load_row(j0, fwa, fpa, ga);
-  for (int j = j0; j < j1; j += 2) {
-    body(j, fwa, fpa, ga, fwb, fpb, gb);
-    if (j + 1 < j1) body(j + 1, fwb, fpb, gb, fwa, fpa, ga);
-  }
+  dst[o] = fmaf(fw[0], keep_w, om_w * (m.rw - 2.0f * sw));
+  dst[(size_t)kQ * L.plane + o] = fmaf(fp[0], keep_p, om_p * (m.rp - 2.0f * sp));
+  dst[(size_t)(2 * kQ) * L.plane + o] = fmaf(g[0], keep_t, om_t * (m.th - 2.0f * sg));
 }
 
 // ---- the fused step, tile variant --------------------------------------------------------------
@@ -411,6 +331,8 @@ __global__ void __launch_bounds__(TX * TY, 2) step_tile_kernel(const StepArgs a)
   }
   float fw[kQ], fp[kQ], g[kQ];
   float hw[kQ], hp[kQ], hg[kQ];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step has completed
   if (active) pull_node<true>(src, L, i, j, fw, fp, g, a.k.inv_nx);
   if (ring) pull_node<false>(src, L, i0 + hx, j0 + hy, hw, hp, hg, a.k.inv_nx);
   if (active) {
@@ -578,6 +500,10 @@ __global__ void __launch_bounds__(kTmaTX * TY, (TY <= 8 ? 2 : 1))
     tma::fence_barrier_init();
     s_abort = 0;
   }
+  // Programmatic dependent launch: let the next step's CTAs start their prologue while this
+  // grid drains, and do not read the state before the previous step has completed.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
 
   // this thread's ring node (tile coordinates, corners excluded)
@@ -887,21 +813,14 @@ int grid_for(int64_t n, int block, int cap) {
 StepConfig choose_step_config(int nx, int ny) {
   StepConfig c;
   // default: TMA-staged tiles for lattices with a few tiles per SM, the plain tile kernel below.
-  // MCLBM_STEP_VARIANT = tile | march | tma overrides (diagnostics and comparisons).
+  // MCLBM_STEP_VARIANT = tile | tma overrides (diagnostics and comparisons).
   c.variant = (nx >= 64 && ny >= 32) ? 2 : 0;
   const char* v = std::getenv("MCLBM_STEP_VARIANT");
   if (v && std::strcmp(v, "tile") == 0) c.variant = 0;
-  if (v && std::strcmp(v, "march") == 0) c.variant = 1;
   if (v && std::strcmp(v, "tma") == 0) c.variant = 2;
   const char* ty = std::getenv("MCLBM_TMA_TILE_Y");
   c.tma_ty = (ty && std::strcmp(ty, "16") == 0) ? 16 : 8;
   c.grid = 0;
-  c.bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
-  const int tiles_x = (nx + c.bx - 1) / c.bx;
-  // aim for at least ~2 CTAs per SM on 152 SMs, with strips of 4 to 32 rows
-  int rows = 32;
-  while (rows > 4 && (int64_t)tiles_x * ((ny + rows - 1) / rows) < 304) rows /= 2;
-  c.rows = rows;
   return c;
 }
 
@@ -954,35 +873,31 @@ cudaError_t make_state_tensor_map(CUtensorMap* map, float* state0, const Layout&
 
 cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                         cudaStream_t st) {
+  // tile and TMA kernels: programmatic dependent launch (the kernel waits on the previous
+  // grid itself with griddepcontrol.wait before it reads the state)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (c.variant == 2) {
     if (!map || c.grid < 1) return cudaErrorInvalidValue;
-    if (c.tma_ty == 16)
-      step_tma_kernel<16><<<c.grid, kTmaTX * 16, TmaTile<16>::SMEM, st>>>(*map, a);
-    else
-      step_tma_kernel<8><<<c.grid, kTmaTX * 8, TmaTile<8>::SMEM, st>>>(*map, a);
-    return cudaGetLastError();
+    cfg.gridDim = dim3(c.grid);
+    if (c.tma_ty == 16) {
+      cfg.blockDim = dim3(kTmaTX * 16);
+      cfg.dynamicSmemBytes = TmaTile<16>::SMEM;
+      return cudaLaunchKernelEx(&cfg, step_tma_kernel<16>, *map, a);
+    }
+    cfg.blockDim = dim3(kTmaTX * 8);
+    cfg.dynamicSmemBytes = TmaTile<8>::SMEM;
+    return cudaLaunchKernelEx(&cfg, step_tma_kernel<8>, *map, a);
   }
-  if (c.variant == 0) {
-    constexpr int TX = 32, TY = 8;
-    dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
-    step_tile_kernel<TX, TY><<<grid, TX * TY, 0, st>>>(a);
-    return cudaGetLastError();
-  }
-  dim3 grid((a.L.nx + c.bx - 1) / c.bx, (a.L.ny + a.rows - 1) / a.rows);
-  switch (c.bx) {
-    case 32:
-      step_kernel<32><<<grid, 32 + 32, 0, st>>>(a);
-      break;
-    case 64:
-      step_kernel<64><<<grid, 64 + 32, 0, st>>>(a);
-      break;
-    case 128:
-      step_kernel<128><<<grid, 128 + 32, 0, st>>>(a);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  constexpr int TX = 32, TY = 8;
+  cfg.gridDim = dim3((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
+  cfg.blockDim = dim3(TX * TY);
+  return cudaLaunchKernelEx(&cfg, step_tile_kernel<TX, TY>, a);
 }
 
 cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
