@@ -150,6 +150,8 @@ __device__ __forceinline__ Moments moments_of(const float* fw, const float* fp, 
 // Steps A2-A7 for one node: moments, forces, drag impulse, collision and store.
 // thE, thW, thN, thS and rpE, ... are the neighbours' theta and rho^p deviations (ghosts
 // already applied by the caller; theta_c's own slope -1/nx is added to d theta/dx here).
+// ALLF: the force mask is known to be MCLBM_F_ALL at compile time (no per-node mask tests).
+template <bool ALLF>
 __device__ __forceinline__ void collide_store(const StepConsts& k, const Layout& L, float* dst,
                                               int i, int j, const float* fw, const float* fp,
                                               const float* g, float thE, float thW, float thN,
@@ -170,7 +172,7 @@ __device__ __forceinline__ void collide_store(const StepConsts& k, const Layout&
   const float inv_rp = has_p ? 1.0f / rp : 0.0f;
   const float upx = has_p ? m.mpx * inv_rp : uwx;
   const float upy = has_p ? m.mpy * inv_rp : uwy;
-  const uint32_t mask = k.mask;
+  const uint32_t mask = ALLF ? MCLBM_F_ALL : k.mask;
 
   // external forces: Boussinesq buoyancy on the fluid, gravity pair (Eq 20, Table 1)
   float Fbuoy = (mask & MCLBM_F_BUOYANCY) ? rho * k.buoy * th : 0.0f;
@@ -295,7 +297,7 @@ __device__ __forceinline__ void collide_store(const StepConsts& k, const Layout&
 // around the tile, all in the same load phase, so each CTA has all its loads in flight at once
 // and the next CTA on the SM overlaps its compute. theta' and rho'^p of the tile and ring go to
 // shared memory; one barrier; then every thread finishes its node.
-template <int TX, int TY>
+template <int TX, int TY, bool ALLF>
 __global__ void __launch_bounds__(TX * TY, 2) step_tile_kernel(const StepArgs a) {
   constexpr int NRING = 2 * TX + 2 * TY;
   static_assert(NRING <= TX * TY, "at most one ring node per thread");
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(TX * TY, 2) step_tile_kernel(const StepArgs a)
   const float rpE = (i + 1 < L.nx) ? s_rp[ty + 1][tx + 2] : rp;
   const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
   const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
-  collide_store(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+  collide_store<ALLF>(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
 }
 
 // ---- the fused step, TMA-staged persistent variant -------------------------------------------
@@ -471,7 +473,7 @@ __device__ __forceinline__ void pull_window(const float* w, const Layout& L, int
   }
 }
 
-template <int TY>
+template <int TY, bool ALLF>
 __global__ void __launch_bounds__(kTmaTX * TY, (TY <= 8 ? 2 : 1))
     step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
   constexpr int TX = kTmaTX;
@@ -581,7 +583,8 @@ __global__ void __launch_bounds__(kTmaTX * TY, (TY <= 8 ? 2 : 1))
       const float rpE = (i + 1 < L.nx) ? s_rp[ty + 1][tx + 2] : rp;
       const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
       const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
-      collide_store(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+      collide_store<ALLF>(a.k, L, a.dst, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN,
+                          rpS);
     }
     __syncthreads();  // the window and the moment tile are free again
   }
@@ -828,15 +831,18 @@ namespace {
 template <int TY>
 cudaError_t prepare_tma(StepConfig* c, const Layout& L) {
   const size_t smem = TmaTile<TY>::SMEM;
-  cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TY>,
+  cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TY, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_tma_kernel<TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<TY>, kTmaTX * TY,
-                                                    smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<TY, false>,
+                                                    kTmaTX * TY, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int tiles = ((L.nx + kTmaTX - 1) / kTmaTX) * ((L.ny + TY - 1) / TY);
@@ -882,22 +888,26 @@ cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMa
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const bool all = a.k.mask == MCLBM_F_ALL;
   if (c.variant == 2) {
     if (!map || c.grid < 1) return cudaErrorInvalidValue;
     cfg.gridDim = dim3(c.grid);
     if (c.tma_ty == 16) {
       cfg.blockDim = dim3(kTmaTX * 16);
       cfg.dynamicSmemBytes = TmaTile<16>::SMEM;
-      return cudaLaunchKernelEx(&cfg, step_tma_kernel<16>, *map, a);
+      return all ? cudaLaunchKernelEx(&cfg, step_tma_kernel<16, true>, *map, a)
+                 : cudaLaunchKernelEx(&cfg, step_tma_kernel<16, false>, *map, a);
     }
     cfg.blockDim = dim3(kTmaTX * 8);
     cfg.dynamicSmemBytes = TmaTile<8>::SMEM;
-    return cudaLaunchKernelEx(&cfg, step_tma_kernel<8>, *map, a);
+    return all ? cudaLaunchKernelEx(&cfg, step_tma_kernel<8, true>, *map, a)
+               : cudaLaunchKernelEx(&cfg, step_tma_kernel<8, false>, *map, a);
   }
   constexpr int TX = 32, TY = 8;
   cfg.gridDim = dim3((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
   cfg.blockDim = dim3(TX * TY);
-  return cudaLaunchKernelEx(&cfg, step_tile_kernel<TX, TY>, a);
+  return all ? cudaLaunchKernelEx(&cfg, step_tile_kernel<TX, TY, true>, a)
+             : cudaLaunchKernelEx(&cfg, step_tile_kernel<TX, TY, false>, a);
 }
 
 cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
