@@ -56,6 +56,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group). Used for the job time:
+    the slowest rank decides."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world_size, slowest_seconds):
+    """Independent replicas: every rank processes the same number of lattice updates; the job's
+    rate (MLUPS) is all ranks' updates over the slowest rank's time."""
+    return units_per_rank * world_size / slowest_seconds / 1e6
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -264,14 +281,10 @@ def main():
         t_end.record(st)
         torch.cuda.synchronize()
     barrier()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
+    elapsed = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, dist, "cuda")
     step_time = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (args.steps * CH)
-    if dist is not None:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
     lu = nx * ny * CH * args.steps
-    value = lu * ws / elapsed / 1e6
+    value = whole_job_rate(lu, ws, elapsed)
     hbm_peak, peak_kind = peaks()
     achieved = BYTES_PER_LU * nx * ny / step_time / 1e9
 
@@ -286,12 +299,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_cav.run_host(warm, CH, 0xFF, fields_host)
-    e2e_time = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_time = float(tt.item())
-    e2e_value = nx * ny * CH * args.steps * ws / e2e_time / 1e6
+    e2e_time = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = whole_job_rate(nx * ny * CH * args.steps, ws, e2e_time)
 
     extras = {}
     if not args.no_extras and rank == 0:
