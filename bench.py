@@ -30,6 +30,7 @@ import workloads  # noqa: E402
 METRIC = "MLUPS & HBM GB/s fraction per MCLBM step; wall time to steady Nu (1e-4)"
 UNIT = "MLUPS"
 BYTES_PER_LU = 216  # 27 FP32 populations read + 27 written per lattice-node update
+STORAGE = {"f32": (0, 216), "f16": (1, 108), "bf16": (2, 108)}  # (code, bytes per update)
 CHUNK = 1000        # time steps per benchmark step (one residual / Nusselt check interval)
 OUR_KERNELS_PER_REDUCTION = 5  # nusselt, residual + final, mass + final
 WORKLOADS = {"cavity256": workloads.CAVITY_256, "cavity1024": workloads.CAVITY_1024}
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--workload", default="cavity256", choices=sorted(WORKLOADS))
     ap.add_argument("--chunk", type=int, default=CHUNK,
                     help="time steps per benchmark step (default: one 1000-step check interval)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage (16-bit: stochastic rounding, FP32 arithmetic)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 1024^2 roofline case, the steady-Nu run and the CPU baseline")
     return ap.parse_args()
@@ -192,10 +195,10 @@ def cpu_baseline(seconds=10.0):
 
 
 def ncu_traffic(workload_name):
-    """DRAM bytes per step launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    """DRAM bytes per step launch (FP32 storage) from the committed ncu summary, if it was
+    taken on the current step-kernel source (else None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1511_04552_gb300", "csrc", "mclbm_kernels.cu")
+    src = os.path.join(ROOT, "paper_1511_04552_gb300", "csrc", "mclbm_device.cuh")
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -249,7 +252,8 @@ def main():
     w = WORKLOADS[args.workload]
     CH = args.chunk
     nx, ny = w["nx"], w["ny"]
-    cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    store, bytes_lu = STORAGE[args.storage]
+    cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"], storage=store)
     cav.init()
     st = cav.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -286,13 +290,13 @@ def main():
     lu = nx * ny * CH * args.steps
     value = whole_job_rate(lu, ws, elapsed)
     hbm_peak, peak_kind = peaks()
-    achieved = BYTES_PER_LU * nx * ny / step_time / 1e9
+    achieved = bytes_lu * nx * ny / step_time / 1e9
 
     # end to end through the C ABI with host buffers: H2D warm fields, init, 1000 steps,
     # all 8 fields and the Nusselt numbers back to the host
     warm = torch.from_numpy(workloads.perturbed_rest_fields(nx, ny, w["phi"], seed=1)).pin_memory()
     fields_host = torch.empty((8, ny, nx), dtype=torch.float32).pin_memory()
-    e2e_cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    e2e_cav = m.Cavity(nx, ny, w["Ra"], w["Pr"], w["phi"], w["d_p"], storage=store)
     for _ in range(max(1, args.warmup)):
         e2e_cav.run_host(warm, CH, 0xFF, fields_host)
     barrier()
@@ -335,6 +339,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "storage": args.storage,
             "data": "synthetic",
             "config": {"workload": w["name"], "nx": nx, "ny": ny, "Ra": w["Ra"], "Pr": w["Pr"],
                        "phi": w["phi"], "d_p": w["d_p"], "time_steps_per_bench_step": CH,
@@ -342,9 +347,10 @@ def main():
                        "l2": "flushed between bench steps (256 MiB write); state %.0f MB" % (
                            2 * 27 * 4 * nx * ny / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": ncu_traffic(w["name"]),
+                         "frac": achieved / hbm_peak,
+                         "traffic": ncu_traffic(w["name"]) if args.storage == "f32" else None,
                          "peak_kind": peak_kind,
-                         "kernel": "step_kernel", "bytes_per_launch": BYTES_PER_LU * nx * ny,
+                         "kernel": "step_tma_kernel", "bytes_per_launch": bytes_lu * nx * ny,
                          "launch_us": step_time * 1e6},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * nx * ny * 4,

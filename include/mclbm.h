@@ -66,8 +66,13 @@ extern "C" {
 #define MCLBM_INIT_REST 0 /* rest, uniform phi, theta linear from +1/2 (hot) to -1/2 (cold) */
 #define MCLBM_INIT_WARM 2 /* equilibrium of caller fields [4][ny][nx]: ux, uy, theta, phi */
 
-/* ---- storage of the populations ---------------------------------------------------------- */
-#define MCLBM_STORE_F32 0
+/* ---- storage of the populations (deviations from the initial conduction state) ----------- */
+#define MCLBM_STORE_F32 0  /* 216 bytes per lattice update */
+#define MCLBM_STORE_F16 1  /* 2^12 x deviation in FP16, 108 bytes per lattice update */
+#define MCLBM_STORE_BF16 2 /* 2^12 x deviation in BF16, 108 bytes per lattice update */
+/* rounding of 16-bit stores (arithmetic is FP32 either way) */
+#define MCLBM_ROUND_STOCHASTIC 0 /* unbiased random rounding (default) */
+#define MCLBM_ROUND_NEAREST 1    /* round to nearest even */
 
 /* Material and model parameters, SI units. mclbm_props_default gives water at 25 C and
  * alumina particles (the paper prints no property values). */
@@ -80,7 +85,8 @@ typedef struct mclbm_props {
   double l_f;                            /* base-fluid molecular mean free path d_f (Eq 10) */
   double Ma;                             /* lattice buoyancy velocity U0 / c_s, 0 < Ma <= 0.5 */
   uint32_t force_mask;                   /* MCLBM_F_* bits */
-  int32_t storage;                       /* MCLBM_STORE_F32 */
+  int32_t storage;                       /* MCLBM_STORE_F32, _F16 or _BF16 */
+  int32_t rounding;                      /* MCLBM_ROUND_*: 16-bit stores only */
 } mclbm_props;
 
 /* Derived create-time constants (FP64), for inspection and tests. Ratios are suspension over
@@ -101,7 +107,7 @@ typedef struct mclbm_consts {
 typedef struct mclbm mclbm_t; /* opaque handle */
 
 /* Fills *p with the defaults (water / alumina, T0 298.15 K, dT 10 K, g 9.81, l_f 0.17 nm,
- * Ma 0.1, all forces, FP32 storage). */
+ * Ma 0.1, all forces, FP32 storage, stochastic rounding for 16-bit storage). */
 void mclbm_props_default(mclbm_props *p);
 
 /* Creates a handle for an nx x ny cavity (2 <= nx, ny <= 32768) at Rayleigh number Ra and

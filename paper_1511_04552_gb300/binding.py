@@ -17,7 +17,8 @@ F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY
 F_ALL = 127
 UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
 INIT_REST, INIT_WARM = 0, 2
-STORE_F32 = 0
+STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
+ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
 GRAPH_STEPS = 64
 
 # every entry point declared in include/mclbm.h
@@ -32,7 +33,7 @@ class Props(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "rho_f", "cp_f", "k_f", "beta_f", "mu_f", "rho_p", "cp_p", "k_p", "beta_p",
         "T0_K", "dT_K", "g", "l_f", "Ma")] + [("force_mask", C.c_uint32),
-                                              ("storage", C.c_int32)]
+                                              ("storage", C.c_int32), ("rounding", C.c_int32)]
 
 
 CONST_NAMES = (

@@ -25,13 +25,14 @@ struct mclbm {
   size_t buf_bytes = 0;
   cudaStream_t stream = nullptr;
   int device = -1;
-  float* state[2] = {nullptr, nullptr};
+  char* state[2] = {nullptr, nullptr};  // two time levels, element type of L.storage
   float* snap = nullptr;     // [4][ny][nx]
   float* staging = nullptr;  // [8][ny][nx]
   double* partials = nullptr;
   double* red = nullptr;
-  int* err_dev = nullptr;  // device error word of the step kernels (bounded waits)
-  CUtensorMap tmap;        // two-level state for the TMA step kernel
+  int* err_dev = nullptr;       // device error word of the step kernels (bounded waits)
+  uint32_t* epoch = nullptr;    // graph replay counter seeding 16-bit stochastic rounding
+  CUtensorMap tmap;             // two-level state for the TMA step kernel
   int cur = 0;
   bool initialised = false;
   bool diverged = false;
@@ -75,7 +76,7 @@ Regions regions(const mclbm_t* h) {
   const size_t n = (size_t)h->nx * h->ny;
   size_t off = 0;
   r.state = off;
-  off += align_up(2 * (size_t)kPlanes * h->L.plane * sizeof(float), 256);
+  off += align_up(2 * (size_t)kPlanes * h->L.plane * h->L.elem, 256);
   r.snap = off;
   off += align_up(4 * n * sizeof(float), 256);
   r.staging = off;
@@ -109,11 +110,13 @@ void drop_graphs(mclbm_t* h) {
     }
 }
 
-StepArgs step_args(const mclbm_t* h, int from) {
+StepArgs step_args(const mclbm_t* h, int from, uint32_t seed) {
   StepArgs a;
   a.src = h->state[from];
   a.dst = h->state[1 - from];
   a.L = h->L;
+  a.seed = seed;
+  a.epoch = h->epoch;
   a.z_src = from * kPlanes;
   a.err = h->err_dev;
   a.k = h->k;
@@ -127,7 +130,9 @@ int build_graph(mclbm_t* h, int from) {
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
-    le = launch_step(step_args(h, (from + s) & 1), h->cfg, &h->tmap, h->cap_stream);
+    le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, &h->tmap, h->cap_stream);
+  // a new stochastic-rounding epoch for the next replay
+  if (le == cudaSuccess) le = launch_epoch_advance(h->epoch, h->cap_stream);
   cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -189,7 +194,11 @@ int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
     if (!(std::isfinite(v) && v > 0)) return MCLBM_EPARAM;
   if (!(p.beta_p >= 0) || !(p.Ma > 0 && p.Ma <= 0.5)) return MCLBM_EPARAM;
   if (p.force_mask & ~MCLBM_F_ALL) return MCLBM_EINVAL;
-  if (p.storage != MCLBM_STORE_F32) return MCLBM_EINVAL;
+  if (p.storage != MCLBM_STORE_F32 && p.storage != MCLBM_STORE_F16 &&
+      p.storage != MCLBM_STORE_BF16)
+    return MCLBM_EINVAL;
+  if (p.rounding != MCLBM_ROUND_STOCHASTIC && p.rounding != MCLBM_ROUND_NEAREST)
+    return MCLBM_EINVAL;
   mclbm_t* h = new (std::nothrow) mclbm();
   if (!h) return MCLBM_EINVAL;
   h->nx = nx;
@@ -207,7 +216,9 @@ int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
   h->k = fold_step_consts(nx, ny, phi, d_p, p, h->c);
   h->L.nx = nx;
   h->L.ny = ny;
-  h->L.pitch = (int)align_up((size_t)nx, 32);
+  h->L.storage = p.storage;
+  h->L.elem = p.storage == MCLBM_STORE_F32 ? 4 : 2;
+  h->L.pitch = (int)align_up((size_t)nx, 128 / h->L.elem);  // 128-byte rows
   h->L.plane = (size_t)h->L.pitch * ny;
   h->cfg = choose_step_config(nx, ny);
   *out = h;
@@ -246,24 +257,26 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->buf = static_cast<char*>(dev_buf);
   h->buf_bytes = bytes;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
-  h->state[0] = reinterpret_cast<float*>(h->buf + r.state);
-  h->state[1] = h->state[0] + (size_t)kPlanes * h->L.plane;
+  h->state[0] = h->buf + r.state;
+  h->state[1] = h->state[0] + (size_t)kPlanes * h->L.plane * h->L.elem;
   h->snap = reinterpret_cast<float*>(h->buf + r.snap);
   h->staging = reinterpret_cast<float*>(h->buf + r.staging);
   h->partials = reinterpret_cast<double*>(h->buf + r.partials);
   h->red = reinterpret_cast<double*>(h->buf + r.red);
   h->err_dev = reinterpret_cast<int*>(h->buf + r.err);
+  h->epoch = reinterpret_cast<uint32_t*>(h->buf + r.err + 4);
   // device-dependent set-up of the step kernel; the TMA variant falls back to the plain tile
   // kernel if the device cannot run it
   h->cfg = choose_step_config(h->nx, h->ny);
+  h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
   if (h->cfg.variant == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
-        make_state_tensor_map(&h->tmap, h->state[0], h->L, h->cfg.tma_ty) != cudaSuccess) {
+        make_state_tensor_map(&h->tmap, h->state[0], h->L) != cudaSuccess) {
       cudaGetLastError();
       h->cfg.variant = 0;
     }
   }
-  CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+  CK(h, cudaMemsetAsync(h->err_dev, 0, 2 * sizeof(int), h->stream));
   h->cur = 0;
   h->initialised = false;
   h->diverged = false;
@@ -304,7 +317,8 @@ int mclbm_step(mclbm_t* h, int64_t n) {
     h->steps += kGraphSteps;
   }
   for (; left > 0; --left) {
-    CK(h, launch_step(step_args(h, h->cur), h->cfg, &h->tmap, h->stream));
+    CK(h, launch_step(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg, &h->tmap,
+                      h->stream));
     h->cur ^= 1;
     h->steps += 1;
   }

@@ -44,16 +44,20 @@ struct StepConsts {
 
 // Layout of the state inside the caller's buffer: 27 planes [ny][pitch] per time level.
 struct Layout {
-  int nx, ny, pitch;  // pitch: floats per row, a multiple of 32 (128 bytes)
-  size_t plane;       // floats per plane = pitch * ny
+  int nx, ny, pitch;  // pitch: elements per row, rows 128-byte aligned
+  size_t plane;       // elements per plane = pitch * ny
+  int storage;        // MCLBM_STORE_F32, _F16 or _BF16
+  int elem;           // bytes per element (4 or 2)
 };
 
 struct StepArgs {
-  const float* src;
-  float* dst;
+  const void* src;  // state level read (element type of L.storage)
+  void* dst;        // state level written
   Layout L;
   int z_src;  // TMA kernel: first plane of the source level in the two-level tensor (0 or 27)
   int* err;   // device error word: bit 0 set when a bounded wait gave up
+  uint32_t seed;             // 16-bit stochastic rounding: per-launch seed
+  const uint32_t* epoch;     // 16-bit stochastic rounding: graph replay counter (device)
   StepConsts k;
 };
 
@@ -67,34 +71,47 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
   int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles
-  int tma_ty;   // TMA kernel: tile height (8 or 16; the tile is 32 wide)
   int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
+  bool sr;      // 16-bit storage: stochastic rounding (else round to nearest)
 };
 StepConfig choose_step_config(int nx, int ny);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
 // may fall back to variant 0. Needs the device current.
 cudaError_t prepare_step(StepConfig* c, const Layout& L);
 // Tensor map of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernel.
-cudaError_t make_state_tensor_map(CUtensorMap* map, float* state0, const Layout& L, int tile_ty);
+cudaError_t make_state_tensor_map(CUtensorMap* map, void* state0, const Layout& L);
 cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                         cudaStream_t st);
-cudaError_t launch_stream_only(const float* src, float* dst, const Layout& L, const StepConsts& k,
+// Per storage type (mclbm_step_f32.cu, mclbm_step_f16.cu, mclbm_step_bf16.cu).
+cudaError_t launch_step_f32(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                            cudaStream_t st);
+cudaError_t launch_step_f16(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                            cudaStream_t st);
+cudaError_t launch_step_bf16(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                             cudaStream_t st);
+cudaError_t prepare_tma_f32(StepConfig* c, const Layout& L);
+cudaError_t prepare_tma_f16(StepConfig* c, const Layout& L);
+cudaError_t prepare_tma_bf16(StepConfig* c, const Layout& L);
+// Advances the stochastic-rounding epoch by one (a single thread; captured after each graph).
+cudaError_t launch_epoch_advance(uint32_t* epoch, cudaStream_t st);
+cudaError_t launch_stream_only(const void* src, void* dst, const Layout& L, const StepConsts& k,
                                cudaStream_t st);
-cudaError_t launch_init(float* dst, const Layout& L, const StepConsts& k, const float* warm,
+cudaError_t launch_init(void* dst, const Layout& L, const StepConsts& k, const float* warm,
                         cudaStream_t st);
-cudaError_t launch_fields(const float* src, const Layout& L, const StepConsts& k, uint32_t which,
+cudaError_t launch_fields(const void* src, const Layout& L, const StepConsts& k, uint32_t which,
                           float* out, cudaStream_t st);
 // Nusselt partial sums: red[0] = sum_j (8 T_h - 9 th_0 + th_1) / 3, red[1] = cold-wall twin.
-cudaError_t launch_nusselt(const float* src, const Layout& L, const StepConsts& k, double* red,
+cudaError_t launch_nusselt(const void* src, const Layout& L, const StepConsts& k, double* red,
                            cudaStream_t st);
 // Mass: red[0] = sum of f^w deviations, red[1] = sum of f^p deviations.
-cudaError_t launch_mass(const float* src, const Layout& L, double* partials, double* red,
+cudaError_t launch_mass(const void* src, const Layout& L, double* partials, double* red,
                         cudaStream_t st);
 // Residual sums red[0..5] = |du|^2, |u|^2, dtheta^2, theta^2, dphi^2, phi^2 against snap;
 // the snapshot [4][ny][nx] (ux, uy, theta, phi) is replaced.
-cudaError_t launch_residual(const float* src, const Layout& L, const StepConsts& k, float* snap,
+cudaError_t launch_residual(const void* src, const Layout& L, const StepConsts& k, float* snap,
                             bool sums, double* partials, double* red, cudaStream_t st);
-cudaError_t launch_state_copy(const float* src, float* dst, const Layout& L, bool to_packed,
+// to_packed: stored level -> packed FP32 deviations [27][ny][nx]; else the reverse.
+cudaError_t launch_state_copy(const void* src, void* dst, const Layout& L, bool to_packed,
                               cudaStream_t st);
 
 }  // namespace mcl

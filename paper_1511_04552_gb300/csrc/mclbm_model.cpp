@@ -37,6 +37,7 @@ void props_default(mclbm_props* p) {
   p->Ma = 0.1;
   p->force_mask = MCLBM_F_ALL;
   p->storage = MCLBM_STORE_F32;
+  p->rounding = MCLBM_ROUND_STOCHASTIC;
 }
 
 int derive_consts(int nx, int ny, double Ra, double Pr, double phi, double d_p,

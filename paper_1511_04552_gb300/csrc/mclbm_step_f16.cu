@@ -1,0 +1,14 @@
+// Step kernels of libmclbm for state storage type __half (one translation unit per storage
+// type, so the build compiles them in parallel).
+#include "mclbm_device.cuh"
+
+namespace mcl {
+
+cudaError_t launch_step_f16(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                           cudaStream_t st) {
+  return launch_step_t<__half>(a, c, map, st);
+}
+
+cudaError_t prepare_tma_f16(StepConfig* c, const Layout& L) { return prepare_tma_t<__half>(c, L); }
+
+}  // namespace mcl

@@ -1,0 +1,14 @@
+// Step kernels of libmclbm for state storage type float (one translation unit per storage
+// type, so the build compiles them in parallel).
+#include "mclbm_device.cuh"
+
+namespace mcl {
+
+cudaError_t launch_step_f32(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
+                           cudaStream_t st) {
+  return launch_step_t<float>(a, c, map, st);
+}
+
+cudaError_t prepare_tma_f32(StepConfig* c, const Layout& L) { return prepare_tma_t<float>(c, L); }
+
+}  // namespace mcl

@@ -75,7 +75,8 @@ def test_create_rejects(pkg, args, code):
 
 def test_create_rejects_bad_props(pkg):
     for field, val, code in [("Ma", 0.0, -2), ("Ma", 0.7, -2), ("rho_p", -1.0, -2),
-                             ("force_mask", 1024, -1), ("storage", 3, -1), ("mu_f", 0.0, -2)]:
+                             ("force_mask", 1024, -1), ("storage", 3, -1), ("mu_f", 0.0, -2),
+                             ("rounding", 2, -1), ("rounding", -1, -1)]:
         p = pkg.props_default(**{field: val})
         with pytest.raises(pkg.MclbmError) as e:
             pkg.create(16, 16, 1e3, 6.2, 0.01, 2e-8, p)
@@ -102,3 +103,16 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
     assert L.mclbm_last_error(None) == b"NULL handle"
     L.mclbm_destroy(None)
     assert L.mclbm_strerror(-5) == b"MCLBM_EDIVERGED"
+
+
+def test_storage_types_size_the_buffer(pkg):
+    """16-bit storage halves the population planes of the bound buffer."""
+    sizes = {}
+    for storage in (0, 1, 2):
+        h = pkg.create(256, 100, 1e5, 6.2, 0.03, 30e-9, pkg.props_default(storage=storage))
+        try:
+            sizes[storage] = pkg.lib().mclbm_buffer_bytes(h)
+        finally:
+            pkg.lib().mclbm_destroy(h)
+    planes32 = 2 * 27 * 256 * 100 * 4
+    assert sizes[0] - sizes[1] == planes32 // 2 and sizes[1] == sizes[2]
