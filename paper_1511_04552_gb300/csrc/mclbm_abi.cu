@@ -32,7 +32,7 @@ struct mclbm {
   double* red = nullptr;
   int* err_dev = nullptr;       // device error word of the step kernels (bounded waits)
   uint32_t* epoch = nullptr;    // graph replay counter seeding 16-bit stochastic rounding
-  CUtensorMap tmap;             // two-level state for the TMA step kernel
+  CUtensorMap tmap[2];          // two-level state for the TMA step kernel: loads, stores
   int cur = 0;
   bool initialised = false;
   bool diverged = false;
@@ -130,7 +130,7 @@ int build_graph(mclbm_t* h, int from) {
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
-    le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, &h->tmap, h->cap_stream);
+    le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, h->tmap, h->cap_stream);
   // a new stochastic-rounding epoch for the next replay
   if (le == cudaSuccess) le = launch_epoch_advance(h->epoch, h->cap_stream);
   cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
@@ -271,7 +271,7 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
   if (h->cfg.variant == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
-        make_state_tensor_map(&h->tmap, h->state[0], h->L) != cudaSuccess) {
+        make_state_tensor_map(h->tmap, h->state[0], h->L) != cudaSuccess) {
       cudaGetLastError();
       h->cfg.variant = 0;
     }
@@ -317,7 +317,7 @@ int mclbm_step(mclbm_t* h, int64_t n) {
     h->steps += kGraphSteps;
   }
   for (; left > 0; --left) {
-    CK(h, launch_step(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg, &h->tmap,
+    CK(h, launch_step(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg, h->tmap,
                       h->stream));
     h->cur ^= 1;
     h->steps += 1;

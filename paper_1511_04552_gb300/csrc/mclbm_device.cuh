@@ -143,6 +143,16 @@ __device__ __forceinline__ uint32_t plane_bits(uint32_t seed, int p) {
   return (seed + (uint32_t)p * 0x9E3779B9u) * 0x85EBCA6Bu;
 }
 
+// Writes one node's 27 results into a [27][STRIDE] shared-memory tile (TMA-stored afterwards).
+template <class T, bool SR, int STRIDE>
+struct TileSink {
+  T* base;        // tile + node offset
+  uint32_t seed;  // per-node rounding stream (SR only)
+  __device__ __forceinline__ void operator()(int p, float v) const {
+    base[p * STRIDE] = SR ? Elem<T>::put_sr(v, plane_bits(seed, p)) : Elem<T>::put(v);
+  }
+};
+
 // Writes one node's 27 results to a state level in global memory.
 template <class T, bool SR>
 struct StoreSink {
@@ -512,6 +522,24 @@ __device__ __forceinline__ void fence_barrier_init() {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// waits until at most one committed bulk store still has to read its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+// waits until every committed bulk store has completed
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 __device__ __forceinline__ void load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
                                         uint32_t bar) {
   asm volatile(
@@ -533,8 +561,13 @@ struct TmaTile {
   static constexpr int WY = kTmaTY + 4;           // window height: 2 rows each side
   static constexpr int WPLANE = WX * WY;
   static constexpr uint32_t BYTES = (uint32_t)kPlanes * WPLANE * Elem<T>::kBytes;
-  static constexpr size_t SMEM = 2 * (size_t)BYTES;  // dynamic shared memory: two windows
-  static_assert(BYTES % 128 == 0, "the second window stays 128-byte aligned");
+  // 16-bit storage leaves room for two output tiles, written by TMA stores; FP32 stores from
+  // registers (two FP32 windows already fill the shared memory of two CTAs per SM)
+  static constexpr bool STORE_TMA = Elem<T>::kBytes == 2;
+  static constexpr uint32_t OUT_BYTES =
+      STORE_TMA ? (uint32_t)kPlanes * kTmaTX * kTmaTY * Elem<T>::kBytes : 0u;
+  static constexpr size_t SMEM = 2 * (size_t)BYTES + 2 * (size_t)OUT_BYTES;
+  static_assert(BYTES % 128 == 0 && OUT_BYTES % 128 == 0, "buffers stay 128-byte aligned");
 };
 
 // Pull of node (i, j) from a window whose element (wx, wy) of plane p is
@@ -581,11 +614,14 @@ __device__ __forceinline__ void pull_window(const T* w, const Layout& L, int i, 
 
 template <class T, bool SR, bool ALLF>
 __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
-    step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+    step_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                    const __grid_constant__ CUtensorMap tmap_out, const StepArgs a) {
   constexpr int TX = kTmaTX, TY = kTmaTY;
   constexpr int NRING = 2 * TX + 2 * TY;
   constexpr int XO = TmaTile<T>::XO;
   constexpr uint32_t BYTES = TmaTile<T>::BYTES;
+  constexpr uint32_t OUT_BYTES = TmaTile<T>::OUT_BYTES;
+  constexpr bool STORE_TMA = TmaTile<T>::STORE_TMA;
   static_assert(NRING <= TX * TY, "at most one ring node per thread");
   extern __shared__ __align__(128) unsigned char win_raw[];
   __shared__ float s_th[TY + 2][TX + 2];
@@ -632,11 +668,18 @@ __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
     }
   }
 
+  // tile coordinates, advanced by gridDim.x tiles per iteration without divisions
+  const int step_y = (int)gridDim.x / tiles_x, step_x = (int)gridDim.x - step_y * tiles_x;
   int tile = blockIdx.x;
+  int tcx = tile % tiles_x, tcy = tile / tiles_x;            // current tile
+  int ncx = tcx + step_x, ncy = tcy + step_y;                // next tile
+  if (ncx >= tiles_x) {
+    ncx -= tiles_x;
+    ++ncy;
+  }
   if (t == 0 && tile < n_tiles) {
     tma::mbar_expect_tx(bar0, BYTES);
-    tma::load_3d(win0, &tmap, (tile % tiles_x) * TX - XO, (tile / tiles_x) * TY - 2, a.z_src,
-                 bar0);
+    tma::load_3d(win0, &tmap, tcx * TX - XO, tcy * TY - 2, a.z_src, bar0);
   }
   for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
     const int stage = it & 1;
@@ -646,12 +689,13 @@ __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
       tma::fence_proxy_async();
       const uint32_t bar = bar0 + 8u * (stage ^ 1);
       tma::mbar_expect_tx(bar, BYTES);
-      tma::load_3d(win0 + (stage ^ 1) * BYTES, &tmap, (next % tiles_x) * TX - XO,
-                   (next / tiles_x) * TY - 2, a.z_src, bar);
+      tma::load_3d(win0 + (stage ^ 1) * BYTES, &tmap, ncx * TX - XO, ncy * TY - 2, a.z_src, bar);
     }
+    // this stage's output tile was last read by the TMA store of two iterations ago
+    if (STORE_TMA && t == 0) tma::bulk_wait_read_1();
     const bool ok = tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
     const T* w = reinterpret_cast<const T*>(win_raw + stage * BYTES);
-    const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
+    const int i0 = tcx * TX, j0 = tcy * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < L.nx && j < L.ny;
     const int gi = i0 + hx, gj = j0 + hy;
@@ -673,6 +717,7 @@ __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
     if (s_abort) {
       if (t == 0) {
         atomicOr(a.err, 1);
+        if (STORE_TMA) tma::bulk_wait_all();
         // drain: this tile's copy and, if issued, the next one (bounded waits)
         tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
         if (next < n_tiles) tma::mbar_wait(bar0 + 8u * (stage ^ 1), ((it + 1) >> 1) & 1);
@@ -691,12 +736,34 @@ __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
       const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
       const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
       const size_t o = (size_t)j * L.pitch + i;
-      StoreSink<T, SR> out{static_cast<T*>(a.dst) + o, L.plane,
-                           SR ? mix32((uint32_t)o ^ sh) : 0u};
-      collide<ALLF>(a.k, L, out, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+      const uint32_t seed = SR ? mix32((uint32_t)o ^ sh) : 0u;
+      if constexpr (STORE_TMA) {
+        T* ob = reinterpret_cast<T*>(win_raw + 2 * BYTES + stage * OUT_BYTES);
+        TileSink<T, SR, TX * TY> out{ob + t, seed};
+        collide<ALLF>(a.k, L, out, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+      } else {
+        StoreSink<T, SR> out{static_cast<T*>(a.dst) + o, L.plane, seed};
+        collide<ALLF>(a.k, L, out, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
+      }
     }
+    if (STORE_TMA) tma::fence_proxy_async();  // generic-proxy writes before the TMA store
     __syncthreads();  // the window and the moment tile are free again
+    if (STORE_TMA && t == 0) {
+      // nodes outside the cavity fall outside the tensor and are not written
+      tma::store_3d(&tmap_out, i0, j0, kPlanes - a.z_src,
+                    win0 + 2 * BYTES + stage * OUT_BYTES);
+      tma::bulk_commit();
+    }
+    tcx = ncx;
+    tcy = ncy;
+    ncx += step_x;
+    ncy += step_y;
+    if (ncx >= tiles_x) {
+      ncx -= tiles_x;
+      ++ncy;
+    }
   }
+  if (STORE_TMA && t == 0) tma::bulk_wait_all();
 }
 
 // ---- host-side launch of the step kernels for one storage type ----------------------------
@@ -734,7 +801,7 @@ cudaError_t launch_step_t3(const StepArgs& a, const StepConfig& c, const CUtenso
     cfg.gridDim = dim3(c.grid);
     cfg.blockDim = dim3(kTmaTX * kTmaTY);
     cfg.dynamicSmemBytes = TmaTile<T>::SMEM;
-    return cudaLaunchKernelEx(&cfg, step_tma_kernel<T, SR, ALLF>, *map, a);
+    return cudaLaunchKernelEx(&cfg, step_tma_kernel<T, SR, ALLF>, map[0], map[1], a);
   }
   cfg.gridDim = dim3((a.L.nx + 31) / 32, (a.L.ny + 7) / 8);
   cfg.blockDim = dim3(256);

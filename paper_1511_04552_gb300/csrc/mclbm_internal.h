@@ -78,8 +78,9 @@ StepConfig choose_step_config(int nx, int ny);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
 // may fall back to variant 0. Needs the device current.
 cudaError_t prepare_step(StepConfig* c, const Layout& L);
-// Tensor map of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernel.
-cudaError_t make_state_tensor_map(CUtensorMap* map, void* state0, const Layout& L);
+// Tensor maps of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernel:
+// maps[0] loads input windows, maps[1] stores output tiles (16-bit storage).
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L);
 cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                         cudaStream_t st);
 // Per storage type (mclbm_step_f32.cu, mclbm_step_f16.cu, mclbm_step_bf16.cu).

@@ -307,7 +307,8 @@ cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMa
   }
 }
 
-cudaError_t make_state_tensor_map(CUtensorMap* map, void* state0, const Layout& L) {
+// maps[0]: window loads (box = window); maps[1]: output tile stores (box = tile).
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -339,10 +340,15 @@ cudaError_t make_state_tensor_map(CUtensorMap* map, void* state0, const Layout& 
   const cuuint64_t dims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)(2 * kPlanes)};
   const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * L.elem, (cuuint64_t)L.plane * L.elem};
   const cuuint32_t box[3] = {(cuuint32_t)wx, (cuuint32_t)(kTmaTY + 4), (cuuint32_t)kPlanes};
+  const cuuint32_t tile[3] = {(cuuint32_t)kTmaTX, (cuuint32_t)kTmaTY, (cuuint32_t)kPlanes};
   const cuuint32_t elem[3] = {1, 1, 1};
-  CUresult r = encode(map, dt, 3, state0, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(&maps[0], dt, 3, state0, dims, strides, box, elem,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  r = encode(&maps[1], dt, 3, state0, dims, strides, tile, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
