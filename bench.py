@@ -214,6 +214,40 @@ def ncu_traffic(workload_name):
         return None
 
 
+def sweep_measure(m, torch, steps=1000, tune_steps=64):
+    """The 80-cavity parametric sweep (sizes 64^2..512^2, Ra x phi x d_p): aggregate MLUPS of
+    one batched persistent launch per time step (autotuned) against stepping each cavity with
+    its own launches one after another, for the same number of steps."""
+    sw = workloads.sweep80()
+    nodes = sum(c["nx"] * c["ny"] for c in sw)
+    cavs = [m.Cavity(c["nx"], c["ny"], c["Ra"], c["Pr"], c["phi"], c["d_p"]).init() for c in sw]
+    batch = m.Batch(cavs)
+    order, per_sm = batch.tune(tune_steps)
+    batch.step(steps)  # warm-up
+    torch.cuda.synchronize()
+    st = batch.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    batch.step(steps)
+    b.record(st)
+    b.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3
+    batch.close()
+    for c in cavs:
+        c.step(steps)  # warm-up (captures each cavity's graphs)
+    torch.cuda.synchronize()
+    a.record(st)
+    for c in cavs:
+        c.step(steps)
+    b.record(st)
+    b.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    return {"workload": "sweep80: %d cavities, %.2f M nodes, sizes 64^2..512^2" % (len(sw), nodes / 1e6),
+            "time_steps": steps, "batched_mlups": nodes * steps / t_batch / 1e6,
+            "sequential_mlups": nodes * steps / t_seq / 1e6, "speedup": t_seq / t_batch,
+            "autotuned": {"tile_order": order, "ctas_per_sm": per_sm}}
+
+
 def time_steps_only(cav, torch, nsteps):
     """Average duration of one step launch: events around back-to-back graph replays."""
     st = cav.stream
@@ -321,6 +355,8 @@ def main():
                          "peak_kind": peak_kind, "bytes_per_launch": BYTES_PER_LU * w4["nx"] * w4["ny"],
                          "launch_us": t_big * 1e6}}
         del big
+        torch.cuda.empty_cache()
+        extras["sweep"] = sweep_measure(m, torch)
         torch.cuda.empty_cache()
         # cold start to steady Nu (1e-4 over two consecutive 1000-step checks)
         w2 = workloads.CAVITY_256

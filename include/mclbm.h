@@ -203,6 +203,47 @@ int mclbm_run_host(mclbm_t *h, const float *warm_host, int64_t n, uint32_t which
 int mclbm_mass_noalloc(const float *state_dev, int nx, int ny, double rho_w0, double rho_p0,
                        double *mass_w, double *mass_p, void *cuda_stream);
 
+/* ---- batches: many cavities per launch (the parametric sweep) ---------------------------- */
+typedef struct mclbm_batch mclbm_batch_t; /* opaque; steps cavities it does not own */
+
+/* Bytes of device memory a batch of the n cavities needs (cavity table, tile table, reduction
+ * scratch); 0 for bad arguments (n outside 1..1023, NULL cavity). */
+size_t mclbm_batch_buffer_bytes(int n, mclbm_t *const *cavities);
+
+/* Groups n bound and initialised cavities (same device, same storage type; nx <= 65535,
+ * ny <= 16383) so that mclbm_batch_step advances all of them with one persistent launch per
+ * time step: the 32 x 8 tiles of every active cavity form one table walked by a grid of 1 or 2
+ * CTAs per SM, each tile streamed into shared memory by TMA as in the single-cavity step
+ * (Eqs 18-19 with Table 1 and Eqs 34-36, per cavity with its own parameters). dev_buf: caller
+ * device memory (>= mclbm_batch_buffer_bytes, 256-byte aligned), cuda_stream: the stream of
+ * every batch call. The cavities stay usable on their own (fields, reductions) between batch
+ * calls; do not step them on their own while they are in a batch. */
+int mclbm_batch_create(int n, mclbm_t *const *cavities, void *dev_buf, size_t bytes,
+                       void *cuda_stream, mclbm_batch_t **out);
+
+/* Advances every active cavity n time steps (n even: each cavity's state returns to the
+ * level it started from), in captured graphs of 64 launches. Async. MCLBM_EINVAL for odd n. */
+int mclbm_batch_step(mclbm_batch_t *b, int64_t n);
+
+/* Hot- and cold-wall Nusselt numbers of every cavity of the batch (host arrays [n]), as
+ * mclbm_nusselt computes them, from one launch. Syncs. */
+int mclbm_batch_nusselt(mclbm_batch_t *b, double *nu_hot, double *nu_cold);
+
+/* Selects which cavities mclbm_batch_step advances (active[c] != 0), e.g. to drop cavities that
+ * have reached a steady state; rebuilds the tile table. Syncs. */
+int mclbm_batch_set_active(mclbm_batch_t *b, const int *active);
+
+/* Autotuner: times steps_per_trial (even) steps for each tile order (0: cavity by cavity,
+ * 1: largest first, 2: interleaved) and 1 or 2 CTAs per SM, keeps the fastest and reports it.
+ * The trial steps are real steps: every active cavity advances 2 x 6 x steps_per_trial. */
+int mclbm_batch_tune(mclbm_batch_t *b, int64_t steps_per_trial, int *order, int *ctas_per_sm);
+
+/* Text of the batch's latest error. */
+const char *mclbm_batch_last_error(const mclbm_batch_t *b);
+
+/* Releases the batch (not the cavities, not the caller's buffer). Waits for its stream. */
+void mclbm_batch_destroy(mclbm_batch_t *b);
+
 /* Derived constants of the handle. */
 int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);
 

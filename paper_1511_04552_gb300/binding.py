@@ -26,7 +26,10 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
            "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
            "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
-           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc")
+           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc",
+           "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
+           "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
+           "mclbm_batch_last_error", "mclbm_batch_destroy")
 
 
 class Props(C.Structure):
@@ -99,6 +102,21 @@ def lib():
         L.mclbm_strerror.restype = C.c_char_p
         L.mclbm_mass_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, vp]
         L.mclbm_mass_noalloc.restype = C.c_int
+        L.mclbm_batch_buffer_bytes.argtypes = [C.c_int, C.POINTER(vp)]
+        L.mclbm_batch_buffer_bytes.restype = C.c_size_t
+        L.mclbm_batch_create.argtypes = [C.c_int, C.POINTER(vp), vp, C.c_size_t, vp,
+                                         C.POINTER(vp)]
+        L.mclbm_batch_step.argtypes = [vp, C.c_int64]
+        L.mclbm_batch_nusselt.argtypes = [vp, dp, dp]
+        L.mclbm_batch_set_active.argtypes = [vp, C.POINTER(C.c_int)]
+        L.mclbm_batch_tune.argtypes = [vp, C.c_int64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.mclbm_batch_last_error.argtypes = [vp]
+        L.mclbm_batch_last_error.restype = C.c_char_p
+        L.mclbm_batch_destroy.argtypes = [vp]
+        L.mclbm_batch_destroy.restype = None
+        for name in ("mclbm_batch_create", "mclbm_batch_step", "mclbm_batch_nusselt",
+                     "mclbm_batch_set_active", "mclbm_batch_tune"):
+            getattr(L, name).restype = C.c_int
         for name in ("mclbm_create", "mclbm_bind", "mclbm_init", "mclbm_step",
                      "mclbm_stream_only", "mclbm_fields", "mclbm_nusselt", "mclbm_mass",
                      "mclbm_residual", "mclbm_state_get", "mclbm_state_set", "mclbm_run_host",
@@ -300,3 +318,104 @@ def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, consecutive=2, max_st
         prev = nh
     return dict(steps=steps, nu_hot=hist[-1][1] if hist else None,
                 nu_cold=hist[-1][2] if hist else None, history=hist, converged=False)
+
+
+class Batch:
+    """Several Cavity objects stepped together, one persistent launch per time step
+    (mclbm_batch_*). Keeps references to its cavities; do not step them alone meanwhile."""
+
+    def __init__(self, cavities, stream=None):
+        import torch
+        self.torch = torch
+        self.cavities = list(cavities)
+        n = len(self.cavities)
+        self._hs = (C.c_void_p * n)(*[c.handle.value for c in self.cavities])
+        nbytes = int(lib().mclbm_batch_buffer_bytes(n, self._hs))
+        if nbytes == 0:
+            raise MclbmError(EINVAL, "mclbm_batch_buffer_bytes")
+        dev = self.cavities[0].device
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = C.c_void_p()
+        rc = lib().mclbm_batch_create(n, self._hs, C.c_void_p(self.buffer.data_ptr()), nbytes,
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != OK:
+            raise MclbmError(rc, "mclbm_batch_create")
+        self._h = h
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise MclbmError(rc, what, lib().mclbm_batch_last_error(self._h).decode())
+
+    def step(self, n):
+        self._check(lib().mclbm_batch_step(self._h, int(n)), "mclbm_batch_step")
+        return self
+
+    def nusselt(self):
+        n = len(self.cavities)
+        a, b = np.zeros(n), np.zeros(n)
+        dp = C.POINTER(C.c_double)
+        self._check(lib().mclbm_batch_nusselt(self._h, a.ctypes.data_as(dp), b.ctypes.data_as(dp)),
+                    "mclbm_batch_nusselt")
+        return a, b
+
+    def set_active(self, active):
+        arr = (C.c_int * len(self.cavities))(*[1 if x else 0 for x in active])
+        self._check(lib().mclbm_batch_set_active(self._h, arr), "mclbm_batch_set_active")
+        return self
+
+    def tune(self, steps_per_trial=200):
+        o, p = C.c_int(), C.c_int()
+        self._check(lib().mclbm_batch_tune(self._h, int(steps_per_trial), C.byref(o), C.byref(p)),
+                    "mclbm_batch_tune")
+        return o.value, p.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mclbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, consecutive=2,
+                    max_steps=1_000_000):
+    """Runs every cavity of a batch until its hot-wall Nusselt number changes by at most tol
+    (relative) between `consecutive` successive checks; converged cavities leave the tile
+    table. Returns per-cavity step counts and final Nusselt numbers."""
+    n = len(batch.cavities)
+    active = [True] * n
+    streak = [0] * n
+    prev = [None] * n
+    done_at = [None] * n
+    steps = 0
+    nu = np.zeros(n)
+    while any(active) and steps < max_steps:
+        batch.step(check_every)
+        steps += check_every
+        hot, _ = batch.nusselt()
+        changed = False
+        for c in range(n):
+            if not active[c]:
+                continue
+            if prev[c] is not None and abs(hot[c] - prev[c]) <= tol * abs(hot[c]):
+                streak[c] += 1
+                if streak[c] >= consecutive:
+                    active[c] = False
+                    done_at[c] = steps
+                    nu[c] = hot[c]
+                    changed = True
+            else:
+                streak[c] = 0
+            prev[c] = hot[c]
+        if changed and any(active):
+            batch.set_active(active)
+    for c in range(n):
+        if done_at[c] is None:
+            nu[c] = prev[c]
+    return dict(steps=done_at, nu_hot=nu, total_steps=steps,
+                converged=all(d is not None for d in done_at))

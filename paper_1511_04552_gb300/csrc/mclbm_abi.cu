@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mclbm_internal.h"
 
@@ -486,6 +487,308 @@ const char* mclbm_strerror(int code) {
     case MCLBM_ETIMEOUT: return "MCLBM_ETIMEOUT";
     default: return "unknown";
   }
+}
+
+}  // extern "C"
+
+// ---- batches -------------------------------------------------------------------------------
+struct mclbm_batch {
+  std::vector<mclbm_t*> cav;
+  std::vector<int> active;
+  std::vector<int> nx, ny;
+  char* buf = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+  BatchCav* d_cavs = nullptr;
+  uint32_t* d_tiles = nullptr;
+  double* d_nu = nullptr;
+  int* d_err = nullptr;
+  uint32_t* d_epoch = nullptr;
+  BatchLaunch bl{};
+  int per_sm_max = 1, sms = 1, per_sm = 2, order = 0;
+  std::vector<uint32_t> table;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t launches = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+int bfail(mclbm_batch_t* b, int code, const char* fmt, ...) {
+  if (b) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define BCK(b, expr)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return bfail((b), MCLBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));            \
+  } while (0)
+
+struct BatchRegions {
+  size_t cavs, tiles, nu, err, total;
+};
+
+BatchRegions batch_regions(int n, mclbm_t* const* cavs) {
+  BatchRegions r;
+  size_t tiles = 0;
+  for (int c = 0; c < n; ++c)
+    tiles += (size_t)((cavs[c]->nx + 31) / 32) * ((cavs[c]->ny + 7) / 8);
+  size_t off = 0;
+  r.cavs = off;
+  off += align_up((size_t)n * sizeof(BatchCav), 256);
+  r.tiles = off;
+  off += align_up(tiles * sizeof(uint32_t), 256);
+  r.nu = off;
+  off += align_up((size_t)n * 2 * sizeof(double), 256);
+  r.err = off;
+  off += 256;
+  r.total = off;
+  return r;
+}
+
+void batch_drop_graph(mclbm_batch_t* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// Uploads the tile table for the current order and active set and sizes the grid.
+int batch_retile(mclbm_batch_t* b) {
+  build_tile_table(b->nx, b->ny, b->active, b->order, &b->table);
+  if (!b->table.empty())
+    BCK(b, cudaMemcpyAsync(b->d_tiles, b->table.data(), b->table.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  b->bl.n_tiles = (int)b->table.size();
+  const int slots = b->per_sm * b->sms;
+  b->bl.grid = b->bl.n_tiles < slots ? b->bl.n_tiles : slots;
+  batch_drop_graph(b);
+  return MCLBM_OK;
+}
+
+int batch_build_graph(mclbm_batch_t* b) {
+  if (!b->cap_stream) BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
+    le = launch_batch_step(b->bl, s & 1, (uint32_t)s, b->cap_stream);
+  if (le == cudaSuccess) le = launch_epoch_advance(b->d_epoch, b->cap_stream);
+  cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
+  if (le != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, MCLBM_ECUDA, "batch graph capture: %s",
+                 cudaGetErrorString(le != cudaSuccess ? le : ee));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    b->graph = nullptr;
+    return bfail(b, MCLBM_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(ie));
+  }
+  return MCLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mclbm_batch_buffer_bytes(int n, mclbm_t* const* cavities) {
+  if (n < 1 || n > 1023 || !cavities) return 0;
+  for (int c = 0; c < n; ++c)
+    if (!cavities[c]) return 0;
+  return batch_regions(n, cavities).total;
+}
+
+int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t bytes,
+                       void* cuda_stream, mclbm_batch_t** out) {
+  if (!out) return MCLBM_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > 1023 || !cavities || !dev_buf) return MCLBM_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(dev_buf) & 255u) != 0) return MCLBM_EINVAL;
+  for (int c = 0; c < n; ++c) {
+    const mclbm_t* h = cavities[c];
+    if (!h || !h->buf || !h->initialised) return MCLBM_ESTATE;
+    if (h->device != cavities[0]->device || h->L.storage != cavities[0]->L.storage)
+      return MCLBM_EINVAL;
+    if (h->nx > 65535 || h->ny > 16383) return MCLBM_EINVAL;
+  }
+  const BatchRegions r = batch_regions(n, cavities);
+  if (bytes < r.total) return MCLBM_EINVAL;
+  mclbm_batch_t* b = new (std::nothrow) mclbm_batch();
+  if (!b) return MCLBM_EINVAL;
+  b->cav.assign(cavities, cavities + n);
+  b->active.assign(n, 1);
+  for (int c = 0; c < n; ++c) {
+    b->nx.push_back(cavities[c]->nx);
+    b->ny.push_back(cavities[c]->ny);
+  }
+  b->buf = static_cast<char*>(dev_buf);
+  b->bytes = bytes;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->device = cavities[0]->device;
+  int rc = MCLBM_OK;
+  auto bail = [&](int code) {
+    mclbm_batch_destroy(b);
+    return code;
+  };
+  if (cudaSetDevice(b->device) != cudaSuccess) return bail(MCLBM_ECUDA);
+  b->d_cavs = reinterpret_cast<BatchCav*>(b->buf + r.cavs);
+  b->d_tiles = reinterpret_cast<uint32_t*>(b->buf + r.tiles);
+  b->d_nu = reinterpret_cast<double*>(b->buf + r.nu);
+  b->d_err = reinterpret_cast<int*>(b->buf + r.err);
+  b->d_epoch = reinterpret_cast<uint32_t*>(b->buf + r.err + 4);
+  std::vector<BatchCav> host(n);
+  bool all = true;
+  for (int c = 0; c < n; ++c) {
+    mclbm_t* h = cavities[c];
+    std::memset(&host[c], 0, sizeof(BatchCav));
+    CUtensorMap maps[2];
+    if (make_state_tensor_map(maps, h->state[0], h->L) != cudaSuccess) return bail(MCLBM_ECUDA);
+    host[c].map = maps[0];
+    host[c].level[0] = h->state[0];
+    host[c].level[1] = h->state[1];
+    host[c].L = h->L;
+    host[c].k = h->k;
+    host[c].cur = h->cur;
+    all = all && h->k.mask == MCLBM_F_ALL;
+  }
+  if (cudaMemcpyAsync(b->d_cavs, host.data(), n * sizeof(BatchCav), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int), b->stream) != cudaSuccess)
+    return bail(MCLBM_ECUDA);
+  if (prepare_batch(cavities[0]->L.storage, &b->per_sm_max) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return bail(MCLBM_ECUDA);
+  if (b->per_sm_max < 1) return bail(MCLBM_ECUDA);
+  b->per_sm = b->per_sm_max < 2 ? b->per_sm_max : 2;
+  b->bl.cavs = b->d_cavs;
+  b->bl.tiles = b->d_tiles;
+  b->bl.storage = cavities[0]->L.storage;
+  b->bl.sr = cavities[0]->props.rounding == MCLBM_ROUND_STOCHASTIC;
+  b->bl.all_forces = all;
+  b->bl.epoch = b->d_epoch;
+  b->bl.err = b->d_err;
+  rc = batch_retile(b);
+  if (rc) return bail(rc);
+  *out = b;
+  return MCLBM_OK;
+}
+
+int mclbm_batch_step(mclbm_batch_t* b, int64_t n) {
+  if (!b) return MCLBM_EINVAL;
+  if (n < 0 || (n & 1)) return bfail(b, MCLBM_EINVAL, "batch step counts must be even");
+  BCK(b, cudaSetDevice(b->device));
+  int64_t left = n;
+  while (left >= kGraphSteps) {
+    if (!b->graph) {
+      int rc = batch_build_graph(b);
+      if (rc) return rc;
+    }
+    BCK(b, cudaGraphLaunch(b->graph, b->stream));
+    left -= kGraphSteps;
+  }
+  for (; left > 0; --left) {
+    BCK(b, launch_batch_step(b->bl, (int)(left & 1), 0x40000000u ^ (uint32_t)b->launches,
+                             b->stream));
+    ++b->launches;
+  }
+  for (size_t c = 0; c < b->cav.size(); ++c)
+    if (b->active[c]) b->cav[c]->steps += n;
+  return MCLBM_OK;
+}
+
+int mclbm_batch_nusselt(mclbm_batch_t* b, double* nu_hot, double* nu_cold) {
+  if (!b || !nu_hot || !nu_cold) return MCLBM_EINVAL;
+  BCK(b, cudaSetDevice(b->device));
+  const int n = (int)b->cav.size();
+  BCK(b, launch_batch_nusselt(b->bl, n, 0, b->d_nu, b->stream));
+  std::vector<double> s(2 * n);
+  int err = 0;
+  BCK(b, cudaMemcpyAsync(s.data(), b->d_nu, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                         b->stream));
+  BCK(b, cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  if (err) return bfail(b, MCLBM_ETIMEOUT, "a batch step kernel gave up a bounded wait");
+  bool finite = true;
+  for (int c = 0; c < n; ++c) {
+    const mclbm_t* h = b->cav[c];
+    const double scale = h->c.k_ratio * (double)h->nx / (double)h->ny;
+    nu_hot[c] = s[2 * c] * scale;
+    nu_cold[c] = s[2 * c + 1] * scale;
+    finite = finite && std::isfinite(nu_hot[c]) && std::isfinite(nu_cold[c]);
+  }
+  if (!finite) return bfail(b, MCLBM_EDIVERGED, "non-finite Nusselt number in the batch");
+  return MCLBM_OK;
+}
+
+int mclbm_batch_set_active(mclbm_batch_t* b, const int* active) {
+  if (!b || !active) return MCLBM_EINVAL;
+  BCK(b, cudaSetDevice(b->device));
+  for (size_t c = 0; c < b->cav.size(); ++c) b->active[c] = active[c] ? 1 : 0;
+  return batch_retile(b);
+}
+
+int mclbm_batch_tune(mclbm_batch_t* b, int64_t steps_per_trial, int* order_out,
+                     int* ctas_per_sm_out) {
+  if (!b || steps_per_trial < 2 || (steps_per_trial & 1)) return MCLBM_EINVAL;
+  BCK(b, cudaSetDevice(b->device));
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_order = b->order, best_per_sm = b->per_sm;
+  int rc = MCLBM_OK;
+  for (int order = 0; order < 3 && rc == MCLBM_OK; ++order)
+    for (int per_sm = 1; per_sm <= b->per_sm_max && per_sm <= 2 && rc == MCLBM_OK; ++per_sm) {
+      b->order = order;
+      b->per_sm = per_sm;
+      if ((rc = batch_retile(b))) break;
+      if ((rc = mclbm_batch_step(b, steps_per_trial))) break;  // warm-up (builds the graph)
+      cudaEventRecord(e0, b->stream);
+      if ((rc = mclbm_batch_step(b, steps_per_trial))) break;
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_order = order;
+        best_per_sm = per_sm;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->order = best_order;
+  b->per_sm = best_per_sm;
+  rc = batch_retile(b);
+  if (order_out) *order_out = best_order;
+  if (ctas_per_sm_out) *ctas_per_sm_out = best_per_sm;
+  return rc;
+}
+
+const char* mclbm_batch_last_error(const mclbm_batch_t* b) { return b ? b->err : "NULL batch"; }
+
+void mclbm_batch_destroy(mclbm_batch_t* b) {
+  if (!b) return;
+  if (b->device >= 0) {
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+  }
+  batch_drop_graph(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
 }
 
 }  // extern "C"

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "mclbm.h"
 
@@ -114,5 +115,31 @@ cudaError_t launch_residual(const void* src, const Layout& L, const StepConsts& 
 // to_packed: stored level -> packed FP32 deviations [27][ny][nx]; else the reverse.
 cudaError_t launch_state_copy(const void* src, void* dst, const Layout& L, bool to_packed,
                               cudaStream_t st);
+
+// ---- batched stepping of many cavities (mclbm_batch.cu) ------------------------------------
+// One cavity of a batch as the batch kernel sees it (device memory, 64-byte aligned).
+struct BatchCav {  // aligned like its CUtensorMap member
+  CUtensorMap map;  // window loads of the cavity's two-level state
+  void* level[2];   // the two state levels
+  Layout L;
+  StepConsts k;
+  int cur;          // level that holds the state at batch creation (even step counts keep it)
+};
+struct BatchLaunch {
+  const void* cavs;   // BatchCav[n]
+  const void* tiles;  // tile table (cavity | tile column | tile row)
+  int n_tiles;
+  int grid;           // persistent CTAs
+  int storage;
+  bool sr, all_forces;
+  const uint32_t* epoch;
+  int* err;
+};
+cudaError_t launch_batch_step(const BatchLaunch& b, int parity, uint32_t seed, cudaStream_t st);
+cudaError_t launch_batch_nusselt(const BatchLaunch& b, int n_cav, int parity, double* out,
+                                 cudaStream_t st);
+cudaError_t prepare_batch(int storage, int* per_sm);
+void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
+                      const std::vector<int>& active, int order, std::vector<uint32_t>* out);
 
 }  // namespace mcl

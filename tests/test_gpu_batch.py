@@ -1,0 +1,92 @@
+"""Batched stepping: several cavities of different sizes and parameters in one persistent
+launch per time step give exactly the states of stepping each cavity alone."""
+import numpy as np
+import pytest
+
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+CASES = [dict(nx=64, ny=64, Ra=1e5, phi=0.03, d_p=30e-9),
+         dict(nx=130, ny=67, Ra=1e4, phi=0.01, d_p=10e-9),
+         dict(nx=96, ny=40, Ra=1e6, phi=0.0, d_p=50e-9),
+         dict(nx=256, ny=256, Ra=1e3, phi=0.04, d_p=100e-9)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.ensure_built()
+
+
+def _cavs(storage=0, **kw):
+    import paper_1511_04552_gb300 as m
+    return [m.Cavity(c["nx"], c["ny"], c["Ra"], 6.2, c["phi"], c["d_p"], storage=storage, **kw)
+            .init() for c in CASES]
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_batch_equals_cavities_alone(storage, monkeypatch):
+    import torch
+    import paper_1511_04552_gb300 as m
+    monkeypatch.setenv("MCLBM_STEP_VARIANT", "tma")
+    alone = _cavs(storage)
+    for c in alone:
+        c.step(266)
+    group = _cavs(storage)
+    b = m.Batch(group)
+    b.step(266)  # 4 graph replays of 64 plus 10 single launches
+    for a, g in zip(alone, group):
+        assert g.steps_done() == 266
+        if storage == 0:
+            assert torch.equal(a.state_get(), g.state_get())
+        else:  # stochastic rounding streams differ; compare fields against each other loosely
+            fa, fg = a.fields(0xFF).cpu().numpy(), g.fields(0xFF).cpu().numpy()
+            assert P.rel_l2(fg[2], fa[2]) < 1e-3
+    hot, cold = b.nusselt()
+    for k, a in enumerate(alone):
+        nh, nc = a.nusselt()
+        if storage == 0:
+            assert abs(hot[k] - nh) <= 1e-12 * abs(nh) and abs(cold[k] - nc) <= 1e-12 * abs(nc)
+
+
+def test_batch_inactive_cavities_do_not_move():
+    import torch
+    import paper_1511_04552_gb300 as m
+    group = _cavs()
+    b = m.Batch(group)
+    b.step(64)
+    before = [c.state_get().clone() for c in group]
+    b.set_active([True, False, True, False])
+    b.step(128)
+    assert torch.equal(group[1].state_get(), before[1])
+    assert torch.equal(group[3].state_get(), before[3])
+    assert not torch.equal(group[0].state_get(), before[0])
+    assert group[0].steps_done() == 192 and group[1].steps_done() == 64
+
+
+def test_batch_tune_and_odd_steps():
+    import paper_1511_04552_gb300 as m
+    group = _cavs()
+    b = m.Batch(group)
+    order, per_sm = b.tune(64)
+    assert order in (0, 1, 2) and per_sm in (1, 2)
+    assert group[0].steps_done() == 2 * 6 * 64
+    with pytest.raises(m.MclbmError):
+        b.step(3)
+    hot, cold = b.nusselt()
+    assert np.all(np.isfinite(hot)) and np.all(hot > 0.9)
+
+
+def test_sweep_to_steady_small():
+    """The steady-state driver on two small cavities: both converge and match their own
+    run_to_steady within the steadiness tolerance."""
+    import paper_1511_04552_gb300 as m
+    cs = [m.Cavity(48, 48, 1e4, 6.2, 0.01, 30e-9).init(),
+          m.Cavity(64, 64, 1e3, 6.2, 0.02, 50e-9).init()]
+    b = m.Batch(cs)
+    res = m.sweep_to_steady(b, tol=1e-4, check_every=1000)
+    assert res["converged"]
+    for k, (nx, Ra, phi, d) in enumerate([(48, 1e4, 0.01, 30e-9), (64, 1e3, 0.02, 50e-9)]):
+        alone = m.Cavity(nx, nx, Ra, 6.2, phi, d).init()
+        r = m.run_to_steady(alone, tol=1e-4, check_every=1000)
+        assert abs(r["nu_hot"] - res["nu_hot"][k]) <= 1e-3 * r["nu_hot"]

@@ -60,3 +60,25 @@ def random_state(nx: int, ny: int, seed: int, amp: float = 1.0) -> np.ndarray:
     """27 planes [27][ny][nx] of float32 uniform noise in [-amp, amp) (streaming tests)."""
     n = 27 * nx * ny
     return (amp * uniform_pm1(seed, 7, n)).astype(np.float32).reshape(27, ny, nx)
+
+
+# Parametric sweep: Ra x phi x d_p, each cavity's resolution drawn from {64, 128, 256, 512}
+# by splitmix64(seed 0, index) mod 4 (80 cavities).
+SWEEP_RA = (1e3, 1e4, 1e5, 1e6)
+SWEEP_PHI = (0.0, 0.01, 0.02, 0.03, 0.04)
+SWEEP_DP = (10e-9, 30e-9, 50e-9, 100e-9)
+SWEEP_SIZES = (64, 128, 256, 512)
+
+
+def sweep80(seed: int = 0):
+    """The 80 cavities of the sweep as dicts (nx, ny, Ra, Pr, phi, d_p), in a fixed order."""
+    out = []
+    idx = 0
+    for Ra in SWEEP_RA:
+        for phi in SWEEP_PHI:
+            for d_p in SWEEP_DP:
+                r = int(splitmix64(np.array([(int(seed) << 32) + idx], dtype=np.uint64))[0])
+                n = SWEEP_SIZES[r % 4]
+                out.append(dict(nx=n, ny=n, Ra=Ra, Pr=6.2, phi=phi, d_p=d_p))
+                idx += 1
+    return out
