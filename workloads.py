@@ -82,3 +82,26 @@ def sweep80(seed: int = 0):
                 out.append(dict(nx=n, ny=n, Ra=Ra, Pr=6.2, phi=phi, d_p=d_p))
                 idx += 1
     return out
+
+
+def random_net_params(segments, seed: int = 0, bias_scale: float = 0.05) -> np.ndarray:
+    """Seeded network parameters (float32) for a list of (name, size, fan_in) segments: weights
+    with fan_in > 0 uniform with the variance of He initialisation (2 / fan_in; 0.1 of that for
+    the last conditioning layer "W2"), biases uniform in [-bias_scale, bias_scale]."""
+    out = []
+    for k, (name, size, fan_in) in enumerate(segments):
+        u = uniform_pm1(seed, 200 + k, size)
+        if fan_in > 0:
+            a = np.sqrt(6.0 / fan_in) * (0.1 if name == "W2" else 1.0)
+            out.append(a * u)
+        else:
+            out.append(bias_scale * u)
+    return np.concatenate(out).astype(np.float32)
+
+
+def random_conditions(n: int, seed: int) -> np.ndarray:
+    """n cavity parameter points [n][3] (Ra, phi, d_p): log10 Ra uniform in [3, 6], phi uniform
+    in [0, 0.05], d_p uniform in [10, 100] nm."""
+    u = 0.5 * (uniform_pm1(seed, 7, 3 * n).reshape(n, 3) + 1.0)
+    return np.stack([10.0 ** (3.0 + 3.0 * u[:, 0]), 0.05 * u[:, 1],
+                     (10.0 + 90.0 * u[:, 2]) * 1e-9], axis=1)
