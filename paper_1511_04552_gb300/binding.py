@@ -29,7 +29,18 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc",
            "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
            "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
-           "mclbm_batch_last_error", "mclbm_batch_destroy")
+           "mclbm_batch_last_error", "mclbm_batch_destroy",
+           # include/mclbm_net.h
+           "mclbm_net_config_default", "mclbm_net_param_count", "mclbm_net_workspace_bytes",
+           "mclbm_net_create", "mclbm_net_destroy", "mclbm_net_last_error", "mclbm_net_bind",
+           "mclbm_net_init_params", "mclbm_net_set_params", "mclbm_net_get_params",
+           "mclbm_net_set_normalizer", "mclbm_net_field_stats", "mclbm_net_forward",
+           "mclbm_net_loss_grad", "mclbm_net_train_step", "mclbm_gemm_bf16")
+
+
+class NetConfig(C.Structure):
+    _fields_ = [("ny", C.c_int32), ("nx", C.c_int32), ("c0", C.c_int32), ("hidden", C.c_int32),
+                ("max_batch", C.c_int32)]
 
 
 class Props(C.Structure):
@@ -116,6 +127,35 @@ def lib():
         L.mclbm_batch_destroy.restype = None
         for name in ("mclbm_batch_create", "mclbm_batch_step", "mclbm_batch_nusselt",
                      "mclbm_batch_set_active", "mclbm_batch_tune"):
+            getattr(L, name).restype = C.c_int
+        ncp = C.POINTER(NetConfig)
+        L.mclbm_net_config_default.argtypes = [ncp]
+        L.mclbm_net_config_default.restype = None
+        L.mclbm_net_param_count.argtypes = [ncp]
+        L.mclbm_net_param_count.restype = C.c_int64
+        L.mclbm_net_workspace_bytes.argtypes = [ncp]
+        L.mclbm_net_workspace_bytes.restype = C.c_size_t
+        L.mclbm_net_create.argtypes = [ncp, C.POINTER(vp)]
+        L.mclbm_net_destroy.argtypes = [vp]
+        L.mclbm_net_destroy.restype = None
+        L.mclbm_net_last_error.argtypes = [vp]
+        L.mclbm_net_last_error.restype = C.c_char_p
+        L.mclbm_net_bind.argtypes = [vp, vp, C.c_size_t, vp]
+        L.mclbm_net_init_params.argtypes = [vp, C.c_uint64]
+        L.mclbm_net_set_params.argtypes = [vp, vp]
+        L.mclbm_net_get_params.argtypes = [vp, vp]
+        L.mclbm_net_set_normalizer.argtypes = [vp, dp, dp]
+        L.mclbm_net_field_stats.argtypes = [vp, C.c_int, vp, dp, dp]
+        L.mclbm_net_forward.argtypes = [vp, C.c_int, vp, vp]
+        L.mclbm_net_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, dp]
+        L.mclbm_net_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
+        L.mclbm_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int64, C.c_int, vp,
+                                      C.c_int64, C.c_int, vp, C.c_int64, C.c_int, C.c_int64,
+                                      C.c_int64, vp]
+        for name in ("mclbm_net_create", "mclbm_net_bind", "mclbm_net_init_params",
+                     "mclbm_net_set_params", "mclbm_net_get_params", "mclbm_net_set_normalizer",
+                     "mclbm_net_field_stats", "mclbm_net_forward", "mclbm_net_loss_grad",
+                     "mclbm_net_train_step", "mclbm_gemm_bf16"):
             getattr(L, name).restype = C.c_int
         for name in ("mclbm_create", "mclbm_bind", "mclbm_init", "mclbm_step",
                      "mclbm_stream_only", "mclbm_fields", "mclbm_nusselt", "mclbm_mass",

@@ -1,0 +1,471 @@
+// CUDA-core kernels of the warm-start network around the tensor-core GEMM (net_gemm.cu):
+// im2col with fused nearest upsampling and channel concatenation, its adjoint (col2im as a
+// gather, so every input gradient is summed in a fixed order), the backward of FiLM + SiLU with
+// the per-channel reductions, the conditioning MLP, the loss, Adam, and small helpers.
+// Activations are channel-major: x[c][b * H * W + y * W + x].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "net_internal.h"
+
+namespace mcl {
+namespace net {
+namespace {
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.f / (1.f + expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+int grid_for(int64_t n, int block, int cap) {
+  int64_t g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// Block sum of NV doubles per thread (blockDim.x == 256), result in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double (*sh)[NV]) {
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += sh[w][k];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---- im2col ---------------------------------------------------------------------------------
+// One thread per (output pixel, group of 8 columns): 16-byte stores of BF16.
+__global__ void im2col_kernel(const Im2colArgs a) {
+  const int kg_n = a.Kp / 8;
+  const int64_t P = (int64_t)a.batch * a.Ho * a.Wo;
+  const int kin = 9 * (a.cu + a.cs);
+  const int H1 = a.up ? a.H / 2 : a.H, W1 = a.up ? a.W / 2 : a.W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * kg_n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int kg = (int)(t % kg_n);
+    const int64_t p = t / kg_n;
+    const int xo = (int)(p % a.Wo);
+    const int yo = (int)((p / a.Wo) % a.Ho);
+    const int b = (int)(p / ((int64_t)a.Wo * a.Ho));
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kg * 8 + j;
+      float x = 0.f;
+      if (k < kin) {
+        const int c = k / 9, tap = k - 9 * c;
+        const int yi = a.stride * yo + tap / 3 - 1, xi = a.stride * xo + tap % 3 - 1;
+        if (yi >= 0 && yi < a.H && xi >= 0 && xi < a.W) {
+          if (c < a.cu) {
+            const int ys = a.up ? yi >> 1 : yi, xs = a.up ? xi >> 1 : xi;
+            x = a.src1[((int64_t)c * a.batch + b) * H1 * W1 + (int64_t)ys * W1 + xs];
+          } else {
+            x = a.src2[((int64_t)(c - a.cu) * a.batch + b) * a.H * a.W + (int64_t)yi * a.W + xi];
+          }
+        }
+      }
+      v[j] = __float2bfloat16_rn(x);
+    }
+    *reinterpret_cast<uint4*>(a.cols + p * a.Kp + kg * 8) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// ---- col2im (gather) ------------------------------------------------------------------------
+// One thread per element of the source: the sum over its (1 or 4) positions in the input grid
+// and over the 3 x 3 taps of the output pixels that read it, in a fixed order.
+__global__ void col2im_kernel(const Col2imArgs a) {
+  const int Hs = a.up ? a.H / 2 : a.H, Ws = a.up ? a.W / 2 : a.W;
+  const int64_t n = (int64_t)a.C * a.batch * Hs * Ws;
+  const int rep = a.up ? 2 : 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int xs = (int)(t % Ws);
+    const int ys = (int)((t / Ws) % Hs);
+    const int64_t cb = t / ((int64_t)Ws * Hs);
+    const int b = (int)(cb % a.batch);
+    const int c = (int)(cb / a.batch);
+    const int cin = a.c_lo + c;
+    float sum = 0.f;
+    for (int dy = 0; dy < rep; ++dy)
+      for (int dx = 0; dx < rep; ++dx) {
+        const int yi = ys * rep + dy, xi = xs * rep + dx;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const int ny = yi + 1 - ky;  // = stride * yo
+          if (ny < 0 || ny % a.stride) continue;
+          const int yo = ny / a.stride;
+          if (yo >= a.Ho) continue;
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const int nxx = xi + 1 - kx;
+            if (nxx < 0 || nxx % a.stride) continue;
+            const int xo = nxx / a.stride;
+            if (xo >= a.Wo) continue;
+            const int64_t p = ((int64_t)b * a.Ho + yo) * a.Wo + xo;
+            sum += a.dcols[p * a.Kp + cin * 9 + ky * 3 + kx];
+          }
+        }
+      }
+    if (a.accumulate)
+      a.dsrc[t] += sum;
+    else
+      a.dsrc[t] = sum;
+  }
+}
+
+// ---- backward of act(film(pre)) ---------------------------------------------------------------
+// One block per (channel, sample).
+__global__ void act_backward_kernel(const ActBwdArgs a) {
+  __shared__ double sh[8][3];
+  const int o = blockIdx.x, b = blockIdx.y;
+  const int64_t P = (int64_t)a.batch * a.hw;
+  float g = 1.f, beta = 0.f;
+  if (a.film) {
+    const float* f = a.film + (int64_t)b * a.film_stride + a.film_off;
+    g = 1.f + f[o];
+    beta = f[a.C + o];
+  }
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int64_t base = (int64_t)o * P + (int64_t)b * a.hw;
+  for (int i = threadIdx.x; i < a.hw; i += blockDim.x) {
+    const float pre = a.pre[base + i];
+    const float dy = a.dy[base + i];
+    const float z = a.film ? g * pre + beta : pre;
+    const float dz = a.act ? dy * dsilu_f(z) : dy;
+    const float dpre = a.film ? dz * g : dz;
+    a.dpre[base + i] = __float2bfloat16_rn(dpre);
+    acc[0] += (double)dpre;
+    acc[1] += (double)dz * (double)pre;
+    acc[2] += (double)dz;
+  }
+  block_sum<3>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* out = a.partial + ((int64_t)o * a.batch + b) * 3;
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+  }
+}
+
+__global__ void bias_film_grad_kernel(const double* partial, int C, int batch, float* dbias,
+                                      float* dfilm, int film_stride, int film_off) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < C; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < batch; ++b) {
+      const double* p = partial + ((int64_t)o * batch + b) * 3;
+      s += p[0];
+      if (dfilm) {
+        dfilm[(int64_t)b * film_stride + film_off + o] = (float)p[1];
+        dfilm[(int64_t)b * film_stride + film_off + C + o] = (float)p[2];
+      }
+    }
+    dbias[o] = (float)s;
+  }
+}
+
+__global__ void splitk_reduce_kernel(const float* part, int splits, int64_t split_stride, int C,
+                                     int kin, int Kp, float* grad) {
+  const int64_t n = (int64_t)C * kin;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(t / kin), k = (int)(t % kin);
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[z * split_stride + (int64_t)o * Kp + k];
+    grad[t] = s;
+  }
+}
+
+__global__ void weights_bf16_kernel(const float* w, int C, int kin, int Kp, __nv_bfloat16* wb) {
+  const int64_t n = (int64_t)C * Kp;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(t / Kp), k = (int)(t % Kp);
+    wb[t] = __float2bfloat16_rn(k < kin ? w[(int64_t)o * kin + k] : 0.f);
+  }
+}
+
+// ---- conditioning MLP (one block; sizes are tiny) ---------------------------------------------
+__global__ void mlp_forward_kernel(const MlpArgs a) {
+  extern __shared__ float sm[];
+  float* c = sm;                    // [batch][3]
+  float* h = sm + 3 * a.batch;      // [batch][H]
+  for (int t = threadIdx.x; t < a.batch; t += blockDim.x) {
+    const float Ra = a.cond_raw[3 * t], phi = a.cond_raw[3 * t + 1], dp = a.cond_raw[3 * t + 2];
+    c[3 * t] = (log10f(Ra) - 4.5f) / 1.5f;
+    c[3 * t + 1] = (phi - 0.025f) / 0.025f;
+    c[3 * t + 2] = (dp * 1e9f - 55.f) / 45.f;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.batch * 3; t += blockDim.x) a.c[t] = c[t];
+  for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) {
+    const int b = t / a.H, j = t % a.H;
+    const float s = a.b1[j] + a.W1[3 * j] * c[3 * b] + a.W1[3 * j + 1] * c[3 * b + 1] +
+                    a.W1[3 * j + 2] * c[3 * b + 2];
+    a.a1[t] = s;
+    h[t] = silu_f(s);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.batch * a.F; t += blockDim.x) {
+    const int b = t / a.F, f = t % a.F;
+    float s = a.b2[f];
+    for (int j = 0; j < a.H; ++j) s += a.W2[(int64_t)f * a.H + j] * h[b * a.H + j];
+    a.r[t] = s;
+  }
+}
+
+__global__ void mlp_backward_kernel(const MlpArgs a, const float* dr, float* gW1, float* gb1,
+                                    float* gW2, float* gb2) {
+  extern __shared__ float sm[];
+  float* h = sm;                    // [batch][H]
+  float* da1 = sm + a.batch * a.H;  // [batch][H]
+  for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) h[t] = silu_f(a.a1[t]);
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.F * a.H; t += blockDim.x) {
+    const int f = t / a.H, j = t % a.H;
+    float s = 0.f;
+    for (int b = 0; b < a.batch; ++b) s += dr[(int64_t)b * a.F + f] * h[b * a.H + j];
+    gW2[t] = s;
+  }
+  for (int f = threadIdx.x; f < a.F; f += blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < a.batch; ++b) s += dr[(int64_t)b * a.F + f];
+    gb2[f] = s;
+  }
+  for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) {
+    const int b = t / a.H, j = t % a.H;
+    float s = 0.f;
+    for (int f = 0; f < a.F; ++f) s += a.W2[(int64_t)f * a.H + j] * dr[(int64_t)b * a.F + f];
+    da1[t] = s * dsilu_f(a.a1[t]);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.H * 3; t += blockDim.x) {
+    const int j = t / 3, i = t % 3;
+    float s = 0.f;
+    for (int b = 0; b < a.batch; ++b) s += da1[b * a.H + j] * a.c[3 * b + i];
+    gW1[t] = s;
+  }
+  for (int j = threadIdx.x; j < a.H; j += blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < a.batch; ++b) s += da1[b * a.H + j];
+    gb1[j] = s;
+  }
+}
+
+// ---- loss -----------------------------------------------------------------------------------
+__global__ void loss_kernel(const LossArgs a) {
+  __shared__ double sh[8][1];
+  const int64_t P = (int64_t)a.batch * a.hw;
+  const int64_t n = 4 * P;
+  const float inv_n2 = (float)(2.0 / (double)n);
+  double acc[1] = {0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(t / P);
+    const int64_t p = t % P;
+    const int b = (int)(p / a.hw);
+    const int64_t i = p % a.hw;
+    const float tgt = (a.target[((int64_t)b * 4 + ch) * a.hw + i] - a.norm[ch]) / a.norm[4 + ch];
+    const float d = a.out[t] - tgt;
+    a.dout[t] = inv_n2 * d;
+    acc[0] += (double)d * (double)d;
+  }
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) a.partial[blockIdx.x] = acc[0] / (double)n;
+}
+
+__global__ void sum_partials_kernel(const double* partial, int n, double* out) {
+  __shared__ double sh[8][1];
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc[0] += partial[i];
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) out[0] = acc[0];
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float gt = g[t];
+    const float mt = b1 * m[t] + (1.f - b1) * gt;
+    const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+    m[t] = mt;
+    v[t] = vt;
+    p[t] -= lr * (mt * c1) / (sqrtf(vt * c2) + eps);
+  }
+}
+
+__global__ void geometry_kernel(float* X, int batch, int ny, int nx) {
+  const int64_t hw = (int64_t)ny * nx, P = batch * hw;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % hw;
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    const float xi = ((float)x + 0.5f) / (float)nx - 0.5f;
+    const float eta = ((float)y + 0.5f) / (float)ny - 0.5f;
+    X[t] = 1.f;
+    X[P + t] = xi;
+    X[2 * P + t] = eta;
+    X[3 * P + t] = 4.f * xi * eta;
+  }
+}
+
+__global__ void denormalize_kernel(const float* out, const float* norm, int batch, int hw,
+                                   float* fields) {
+  const int64_t P = (int64_t)batch * hw, n = 4 * P;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(t / P);
+    const int64_t p = t % P;
+    const int b = (int)(p / hw);
+    const int64_t i = p % hw;
+    fields[((int64_t)b * 4 + ch) * hw + i] = norm[ch] + norm[4 + ch] * out[t];
+  }
+}
+
+// grid (blocks, 4): per channel, block-strided FP64 sums of x and x^2.
+__global__ void field_moments_kernel(const float* fields, int n, int hw, double* partial) {
+  __shared__ double sh[8][2];
+  const int ch = blockIdx.y;
+  const int64_t total = (int64_t)n * hw;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / hw, i = t % hw;
+    const double x = fields[(s * 4 + ch) * hw + i];
+    acc[0] += x;
+    acc[1] += x * x;
+  }
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* o = partial + ((int64_t)ch * gridDim.x + blockIdx.x) * 2;
+    o[0] = acc[0];
+    o[1] = acc[1];
+  }
+}
+
+// p[i] = scale * u, u uniform in [-1, 1) from splitmix64 of (seed, stream, i).
+__global__ void uniform_fill_kernel(float* p, int64_t n, float scale, uint64_t seed,
+                                    uint32_t stream) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = ((seed << 40) ^ ((uint64_t)stream << 32)) + (uint64_t)t;
+    z = (z + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    p[t] = scale * (float)(2.0 * u - 1.0);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_uniform_fill(float* p, int64_t n, float scale, uint64_t seed, uint32_t stream,
+                                cudaStream_t st) {
+  uniform_fill_kernel<<<grid_for(n, 256, 1024), 256, 0, st>>>(p, n, scale, seed, stream);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_im2col(const Im2colArgs& a, cudaStream_t st) {
+  const int64_t n = (int64_t)a.batch * a.Ho * a.Wo * (a.Kp / 8);
+  im2col_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col2im(const Col2imArgs& a, cudaStream_t st) {
+  const int Hs = a.up ? a.H / 2 : a.H, Ws = a.up ? a.W / 2 : a.W;
+  const int64_t n = (int64_t)a.C * a.batch * Hs * Ws;
+  col2im_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_act_backward(const ActBwdArgs& a, cudaStream_t st) {
+  act_backward_kernel<<<dim3(a.C, a.batch), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bias_film_grad(const double* partial, int C, int batch, float* dbias,
+                                  float* dfilm, int film_stride, int film_off, cudaStream_t st) {
+  bias_film_grad_kernel<<<grid_for(C, 128, 64), 128, 0, st>>>(partial, C, batch, dbias, dfilm,
+                                                              film_stride, film_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_reduce(const float* part, int splits, int64_t split_stride, int C,
+                                 int kin, int Kp, float* grad, cudaStream_t st) {
+  splitk_reduce_kernel<<<grid_for((int64_t)C * kin, 256, 1024), 256, 0, st>>>(
+      part, splits, split_stride, C, kin, Kp, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weights_bf16(const float* w, int C, int kin, int Kp, __nv_bfloat16* wb,
+                                cudaStream_t st) {
+  weights_bf16_kernel<<<grid_for((int64_t)C * Kp, 256, 1024), 256, 0, st>>>(w, C, kin, Kp, wb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(const MlpArgs& a, cudaStream_t st) {
+  const size_t sm = sizeof(float) * (size_t)a.batch * (3 + a.H);
+  mlp_forward_kernel<<<1, 256, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_backward(const MlpArgs& a, const float* dr, float* gW1, float* gb1,
+                                float* gW2, float* gb2, cudaStream_t st) {
+  const size_t sm = sizeof(float) * (size_t)a.batch * a.H * 2;
+  mlp_backward_kernel<<<1, 256, sm, st>>>(a, dr, gW1, gb1, gW2, gb2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const LossArgs& a, cudaStream_t st) {
+  loss_kernel<<<a.blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st) {
+  sum_partials_kernel<<<1, 256, 0, st>>>(partial, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t st) {
+  adam_kernel<<<grid_for(n, 256, 1024), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geometry(float* X, int batch, int ny, int nx, cudaStream_t st) {
+  geometry_kernel<<<grid_for((int64_t)batch * ny * nx, 256, 2048), 256, 0, st>>>(X, batch, ny,
+                                                                                  nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_denormalize(const float* out, const float* norm, int batch, int hw,
+                               float* fields, cudaStream_t st) {
+  denormalize_kernel<<<grid_for(4LL * batch * hw, 256, 2048), 256, 0, st>>>(out, norm, batch, hw,
+                                                                            fields);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_moments(const float* fields, int n, int hw, double* partial, int blocks,
+                                 cudaStream_t st) {
+  field_moments_kernel<<<dim3(blocks, 4), 256, 0, st>>>(fields, n, hw, partial);
+  return cudaGetLastError();
+}
+
+}  // namespace net
+}  // namespace mcl

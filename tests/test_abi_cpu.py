@@ -116,3 +116,36 @@ def test_storage_types_size_the_buffer(pkg):
             pkg.lib().mclbm_destroy(h)
     planes32 = 2 * 27 * 256 * 100 * 4
     assert sizes[0] - sizes[1] == planes32 // 2 and sizes[1] == sizes[2]
+
+
+def test_net_config_and_param_count_match_oracle(pkg):
+    """The network's parameter count and layout size from the library (host-only calls) against
+    the oracle's statement of the same network."""
+    import ctypes as C
+    from oracle import warmnet as WN
+    L = pkg.lib()
+    cfg = pkg.binding.NetConfig()
+    L.mclbm_net_config_default(C.byref(cfg))
+    assert (cfg.ny, cfg.nx, cfg.c0, cfg.hidden, cfg.max_batch) == (256, 256, 16, 64, 16)
+    assert L.mclbm_net_param_count(C.byref(cfg)) == WN.param_count(16, 64) == 734148
+    for c0, hid in [(8, 16), (24, 5), (64, 1)]:
+        c = pkg.binding.NetConfig(32, 48, c0, hid, 2)
+        assert L.mclbm_net_param_count(C.byref(c)) == WN.param_count(c0, hid)
+        assert L.mclbm_net_workspace_bytes(C.byref(c)) > 0
+    for bad in [(20, 32, 16, 64, 4), (32, 32, 12, 64, 4), (32, 32, 16, 0, 4), (32, 32, 16, 64, 0),
+                (32, 32, 16, 256, 32), (4096, 4096, 16, 8, 8)]:
+        c = pkg.binding.NetConfig(*bad)
+        assert L.mclbm_net_param_count(C.byref(c)) == 0
+        h = C.c_void_p()
+        assert L.mclbm_net_create(C.byref(c), C.byref(h)) == -1
+    h = C.c_void_p()
+    assert L.mclbm_net_create(C.byref(cfg), C.byref(h)) == 0
+    # no workspace bound: every compute call is refused without touching a device
+    assert L.mclbm_net_forward(h, 1, None, None) == -3
+    assert L.mclbm_net_bind(h, C.c_void_p(256), 16, None) == -1  # too small
+    L.mclbm_net_destroy(h)
+    # the GEMM validates its operands on the host
+    assert L.mclbm_gemm_bf16(128, 128, 60, C.c_void_p(256), 64, 1, C.c_void_p(256), 64, 1,
+                             C.c_void_p(256), 128, 1, 64, 0, None) == -1  # K % 8 != 0
+    assert L.mclbm_gemm_bf16(12, 128, 64, C.c_void_p(256), 64, 0, C.c_void_p(256), 64, 1,
+                             C.c_void_p(256), 128, 1, 64, 0, None) == -1  # MN-major M % 8 != 0

@@ -1,0 +1,188 @@
+"""The warm-start network on the GPU (include/mclbm_net.h) against the FP64 oracle
+(oracle/warmnet.py): the tensor-core GEMM against numpy, the forward pass and the gradient
+against the oracle with the same BF16 operand rounding (tight) and in plain FP64 (loose), Adam's
+first step, determinism and training progress."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import warmnet as WN
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.ensure_built()
+
+
+def _bf16_pair(x):
+    """A host array rounded to bfloat16 (torch's CPU conversion) and the same values as FP64."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16)
+    return t, t.double().numpy()
+
+
+@pytest.mark.parametrize("M,N,K,a_km,b_km,splits", [
+    (128, 128, 64, True, True, 1),
+    (300, 40, 136, True, True, 1),      # ragged M, N and a K tail inside one 64-slice
+    (256, 4, 144, True, True, 1),       # N below the 16-column instruction minimum
+    (1024, 432, 16, False, False, 1),   # both operands MN-major (input-gradient shape)
+    (16, 432, 4096, True, False, 8),    # split K, MN-major B (weight-gradient shape)
+    (4, 40, 2048, True, False, 3),      # M = 4 rows, uneven splits
+    (520, 256, 1000, True, True, 2),
+])
+def test_gemm_matches_numpy(M, N, K, a_km, b_km, splits):
+    import torch
+    from paper_1511_04552_gb300.warmstart import gemm_bf16
+    r = np.random.default_rng(M * 7 + N + K)
+    a = r.normal(size=(M, K) if a_km else (K, M))
+    b = r.normal(size=(N, K) if b_km else (K, N))
+    ta, a64 = _bf16_pair(a)
+    tb, b64 = _bf16_pair(b)
+    A = a64 if a_km else a64.T
+    Bm = b64 if b_km else b64.T
+    kps = ((K + splits - 1) // splits + 63) // 64 * 64
+    d = gemm_bf16(ta.cuda(), tb.cuda(), a_km, b_km, splits=splits, k_per_split=kps)
+    torch.cuda.synchronize()
+    d = d.cpu().numpy().astype(np.float64)
+    total = np.zeros((M, N))
+    for z in range(splits):
+        k0, k1 = z * kps, min(K, (z + 1) * kps)
+        ref = A[:, k0:k1] @ Bm[:, k0:k1].T if k1 > k0 else np.zeros((M, N))
+        scale = np.abs(A[:, k0:k1]) @ np.abs(Bm[:, k0:k1]).T if k1 > k0 else np.ones((M, N))
+        assert np.all(np.abs(d[z] - ref) <= 1e-4 * scale + 1e-30), (z, np.max(np.abs(d[z] - ref)))
+        total += d[z]
+    np.testing.assert_allclose(total, A @ Bm.T, rtol=0, atol=1e-4 * np.max(np.abs(A) @ np.abs(Bm).T))
+
+
+def _net(ny, nx, c0, hidden, batch, seed=0):
+    from paper_1511_04552_gb300.warmstart import WarmNet
+    params = workloads.random_net_params(WN.param_segments(c0, hidden), seed=seed)
+    net = WarmNet(ny, nx, c0, hidden, max_batch=batch)
+    net.set_params(params)
+    return net, params.astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+CONDS = np.array([[2.0e3, 0.010, 20e-9], [3.0e5, 0.045, 90e-9], [8.0e4, 0.0, 55e-9]])
+
+
+@pytest.mark.parametrize("ny,nx,c0,hidden", [(32, 32, 8, 16), (48, 64, 8, 7)])
+def test_forward_matches_oracle(ny, nx, c0, hidden):
+    import torch
+    net, p = _net(ny, nx, c0, hidden, 3)
+    mean, scale = np.array([0.01, -0.02, 0.1, 0.02]), np.array([0.05, 0.04, 0.3, 0.001])
+    net.set_normalizer(mean, scale)
+    out = net.forward(torch.from_numpy(CONDS.astype(np.float32))).cpu().numpy()
+    cond32 = CONDS.astype(np.float32).astype(np.float64)
+    ref = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, bf16=True)
+    ref64 = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden)
+    norm = lambda f: (f - mean[None, :, None, None]) / scale[None, :, None, None]  # noqa: E731
+    e16, e64 = _rel(norm(out), norm(ref)), _rel(norm(out), norm(ref64))
+    print("forward rel L2: vs bf16 oracle %.2e, vs fp64 oracle %.2e" % (e16, e64))
+    assert e16 < 1e-4
+    assert e64 < 3e-2
+
+
+def _check_grads(net, p, ny, nx, c0, hidden, cond, target, mean, scale, tight, loose):
+    import torch
+    net.set_normalizer(mean, scale)
+    loss, g = net.loss_grad(torch.from_numpy(cond.astype(np.float32)), torch.from_numpy(target))
+    g = g.cpu().numpy().astype(np.float64)
+    cond32 = cond.astype(np.float32).astype(np.float64)
+    c = WN.condition(*cond32.T)
+    t64 = target.astype(np.float64)
+    l16, g16 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden, bf16=True)
+    l64, g64 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden)
+    assert abs(loss - l16) < 1e-5 * l16, (loss, l16)
+    assert abs(loss - l64) < 2e-2 * l64, (loss, l64)
+    worst16, worst64 = 0.0, 0.0
+    lay, _ = WN.param_layout(c0, hidden)
+    for name, (o, s) in lay.items():
+        k = int(np.prod(s))
+        e16 = _rel(g[o:o + k], g16[o:o + k])
+        e64 = _rel(g[o:o + k], g64[o:o + k])
+        worst16, worst64 = max(worst16, e16), max(worst64, e64)
+        assert e16 < tight, (name, e16)
+        assert e64 < loose, (name, e64)
+    print("grad worst per-tensor rel L2: vs bf16 oracle %.2e, vs fp64 oracle %.2e" % (worst16,
+                                                                                     worst64))
+
+
+def test_gradient_matches_oracle_small():
+    ny = nx = 32
+    c0, hidden = 8, 16
+    net, p = _net(ny, nx, c0, hidden, 3, seed=2)
+    r = np.random.default_rng(11)
+    target = r.normal(size=(3, 4, ny, nx)).astype(np.float32)
+    mean, scale = np.array([0.1, 0.0, -0.1, 0.5]), np.array([1.0, 2.0, 0.5, 1.5])
+    _check_grads(net, p, ny, nx, c0, hidden, CONDS, target, mean, scale, 2e-3, 6e-2)
+
+
+@pytest.mark.slow
+def test_forward_and_gradient_full_size():
+    """The 256 x 256, c0 16 network of the warm start at batch 1 (one sample: the oracle's FP64
+    convolutions take seconds)."""
+    import torch
+    ny = nx = 256
+    net, p = _net(ny, nx, 16, 64, 2, seed=3)
+    mean, scale = np.zeros(4), np.ones(4)
+    net.set_normalizer(mean, scale)
+    cond = CONDS[1:2]
+    out = net.forward(torch.from_numpy(cond.astype(np.float32))).cpu().numpy()
+    c = WN.condition(*cond.astype(np.float32).astype(np.float64).T)
+    ref, _ = WN.forward(p, c, ny, nx, 16, 64, bf16=True)
+    assert _rel(out, ref) < 1e-4
+    r = np.random.default_rng(12)
+    target = r.normal(size=(1, 4, ny, nx)).astype(np.float32)
+    _check_grads(net, p, ny, nx, 16, 64, cond, target, mean, scale, 2e-3, 6e-2)
+
+
+def test_adam_first_step_and_determinism():
+    """After set_params the first Adam step moves every parameter with a clearly nonzero gradient
+    by lr against the sign of the oracle's gradient; repeated calls are bitwise identical."""
+    import torch
+    ny = nx = 32
+    c0, hidden = 8, 16
+    net, p = _net(ny, nx, c0, hidden, 3, seed=4)
+    r = np.random.default_rng(13)
+    target = torch.from_numpy(r.normal(size=(3, 4, ny, nx)).astype(np.float32))
+    cond = torch.from_numpy(CONDS.astype(np.float32))
+    l1, g1 = net.loss_grad(cond, target)
+    l2, g2 = net.loss_grad(cond, target)
+    assert l1 == l2 and torch.equal(g1, g2)
+    o1 = net.forward(cond).clone()
+    assert torch.equal(o1, net.forward(cond))
+    c = WN.condition(*CONDS.astype(np.float32).astype(np.float64).T)
+    _, g_ref = WN.loss_and_grad(p, c, target.numpy().astype(np.float64), np.zeros(4), np.ones(4),
+                                ny, nx, c0, hidden, bf16=True)
+    lr = 1e-3
+    net.train_step(cond, target, lr)
+    dp = net.get_params().cpu().numpy().astype(np.float64) - p.astype(np.float32).astype(np.float64)
+    big = (np.abs(g_ref) > 1e-2 * np.abs(g_ref).max()) & (np.abs(g_ref) > 1e-4)
+    assert big.sum() > 1000
+    np.testing.assert_allclose(dp[big], -lr * np.sign(g_ref[big]), rtol=1e-3, atol=2e-8)
+
+
+def test_training_reduces_loss():
+    """Fitting two fixed samples: the loss falls by an order of magnitude in 150 steps."""
+    import torch
+    ny = nx = 32
+    from paper_1511_04552_gb300.warmstart import WarmNet
+    net = WarmNet(ny, nx, 8, 16, max_batch=2).init_params(5)
+    xi = (np.arange(nx) + 0.5) / nx - 0.5
+    X, Y = np.meshgrid(xi, xi)
+    f = np.stack([np.stack([np.sin(np.pi * X) * a, np.cos(np.pi * Y) * a, -X * a, X * Y * a])
+                  for a in (1.0, 0.5)]).astype(np.float32)
+    cond = torch.from_numpy(CONDS[:2].astype(np.float32))
+    tgt = torch.from_numpy(f).cuda()
+    net.set_normalizer(*net.field_stats(tgt))
+    losses = [net.train_step(cond, tgt, 3e-3) for _ in range(150)]
+    print("loss %.3e -> %.3e" % (losses[0], losses[-1]))
+    assert losses[-1] < 0.1 * losses[0]
+    assert np.all(np.isfinite(losses))
