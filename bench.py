@@ -248,6 +248,29 @@ def sweep_measure(m, torch, steps=1000, tune_steps=64):
             "autotuned": {"tile_order": order, "ctas_per_sm": per_sm}}
 
 
+WARMNET = os.path.join(ROOT, "paper_1511_04552_gb300", "weights", "warmnet_256.npz")
+
+
+def warm_start_measure(m, torch, n_points=20):
+    """Learned warm start against cold starts on held-out parameter points (256^2, steady Nu to
+    1e-4): both sides solved with the batched solver; the warm side's wall time includes the
+    network's inference."""
+    if not os.path.exists(WARMNET):
+        return {"unavailable": "no trained network weights in the package"}
+    from paper_1511_04552_gb300 import warmstart as W
+    net = W.WarmNet.load(WARMNET)
+    conds = workloads.random_conditions(n_points, seed=2)
+    ev = W.evaluate(net, conds, group=n_points)
+    return {"workload": "%d held-out points, 256^2, log-uniform Ra 1e3..1e6, phi 0..5 %%, "
+                        "d_p 10..100 nm" % n_points,
+            "cold_wall_s": ev["cold_wall_s"], "warm_wall_s": ev["warm_wall_s"],
+            "speedup_wall": ev["speedup_wall"], "speedup_steps": ev["speedup_steps"],
+            "cold_steps_mean": float(ev["cold_steps"].mean()),
+            "warm_steps_mean": float(ev["warm_steps"].mean()),
+            "max_nu_rel_diff": float(ev["nu_rel_diff"].max()),
+            "inference_s": ev["inference_s"]}
+
+
 def time_steps_only(cav, torch, nsteps):
     """Average duration of one step launch: events around back-to-back graph replays."""
     st = cav.stream
@@ -357,6 +380,8 @@ def main():
         del big
         torch.cuda.empty_cache()
         extras["sweep"] = sweep_measure(m, torch)
+        torch.cuda.empty_cache()
+        extras["warm_start"] = warm_start_measure(m, torch)
         torch.cuda.empty_cache()
         # cold start to steady Nu (1e-4 over two consecutive 1000-step checks)
         w2 = workloads.CAVITY_256
