@@ -15,7 +15,8 @@
  *   e0 = conv(X, 4->C0), e1..e3 = stride-2 convs, e4 = stride-2 conv + FiLM;
  *   d3, d2, d1, d0 = conv(cat(up2(previous), skip)) + FiLM;  out = conv(d0, C0->4);
  *   FiLM: gamma = 1 + r[a:a+C], beta = r[a+C:a+2C], r = W2 silu(W1 c + b1) + b2, slices in the
- *   order e4, d3, d2, d1, d0;  fields = mean + scale * out (per-channel normaliser).
+ *   order e4, d3, d2, d1, d0;  fields = mean + scale * out (per-channel normaliser), the phi
+ *   field then shifted to the conditioning phi's mean.
  * Parameters: one flat FP32 vector, per conv layer (e0..e4, d3..d0, out) W[Cout][Cin][3][3]
  *   then b[Cout], then W1[hidden][3], b1[hidden], W2[F][hidden], b2[F], F = 2(C4+C3+C2+C1+C0).
  * Every convolution is an im2col GEMM on the tensor cores with BF16 operands (activations,
@@ -83,7 +84,9 @@ int mclbm_net_set_normalizer(mclbm_net_t* net, const double mean[4], const doubl
 int mclbm_net_field_stats(mclbm_net_t* net, int n, const float* fields_dev, double mean[4],
                           double scale[4]);
 
-/* Predicted fields [batch][4][ny][nx] for cond [batch][3]. async. */
+/* Predicted fields [batch][4][ny][nx] for cond [batch][3]: mean + scale * output, and then the
+ * phi field shifted by a constant so that its cavity mean is the sample's phi (the warm start
+ * carries the particle mass of the cold start). async. */
 int mclbm_net_forward(mclbm_net_t* net, int batch, const float* cond_dev, float* fields_dev);
 
 /* Loss (mean squared error of the normalised output against the normalised target fields) and

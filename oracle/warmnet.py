@@ -29,7 +29,9 @@ below is the one the CUDA path implements independently:
   slices of r in that order.
 * Parameters, one flat FP32 vector: for each conv layer in the order above W [Cout][Cin][3][3]
   then b [Cout]; then W1 [hidden][3], b1 [hidden], W2 [F][hidden], b2 [F], F = 2 (C4+C3+C2+C1+C0).
-* Fields: F_ch = mean_ch + scale_ch * out_ch (per-channel normaliser, not trained).
+* Fields: F_ch = mean_ch + scale_ch * out_ch (per-channel normaliser, not trained); for a
+  warm start the phi field is then shifted by a constant so that its mean over the cavity is
+  the sample's phi (the particle mass is conserved by the solver, so the steady state has it).
   Loss = mean over samples, channels and nodes of (out - (F_target - mean)/scale)^2.
 * Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
@@ -298,9 +300,14 @@ def loss_and_grad(params, cond, fields, mean, scale, ny, nx, c0=16, hidden=64, b
     return loss, backward(params, cache, dout, c0, hidden, bf16=bf16)
 
 
-def predict_fields(params, cond, mean, scale, ny, nx, c0=16, hidden=64, bf16=False):
+def predict_fields(params, cond, mean, scale, ny, nx, c0=16, hidden=64, bf16=False, phi=None):
+    """mean + scale * output; with phi (the samples' volume fractions, [B]) the phi channel is
+    then shifted by a constant per sample so that its cavity mean equals phi."""
     out, _ = forward(params, cond, ny, nx, c0, hidden, bf16=bf16)
-    return np.asarray(mean)[None, :, None, None] + np.asarray(scale)[None, :, None, None] * out
+    f = np.asarray(mean)[None, :, None, None] + np.asarray(scale)[None, :, None, None] * out
+    if phi is not None:
+        f[:, 3] += (np.asarray(phi, dtype=np.float64) - f[:, 3].mean(axis=(1, 2)))[:, None, None]
+    return f
 
 
 def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

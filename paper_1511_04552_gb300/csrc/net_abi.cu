@@ -596,8 +596,8 @@ int mclbm_net_forward(mclbm_net_t* n, int batch, const float* cond, float* field
   if (!cond || !fields) return fail(n, MCLBM_EINVAL, "null pointer");
   cudaError_t e = forward(n, batch, cond);
   if (e == cudaSuccess)
-    e = launch_denormalize(n->L[kNumLayers - 1].pre, n->norm, batch, n->cfg.ny * n->cfg.nx,
-                           fields, n->stream);
+    e = launch_denormalize(n->L[kNumLayers - 1].pre, n->norm, cond, batch,
+                           n->cfg.ny * n->cfg.nx, fields, n->stream);
   return e == cudaSuccess ? MCLBM_OK : cuda_fail(n, e, "mclbm_net_forward");
 }
 

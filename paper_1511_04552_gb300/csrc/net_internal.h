@@ -140,9 +140,10 @@ cudaError_t launch_uniform_fill(float* p, int64_t n, float scale, uint64_t seed,
                                 cudaStream_t st);
 // Geometry input X [4][batch * ny * nx].
 cudaError_t launch_geometry(float* X, int batch, int ny, int nx, cudaStream_t st);
-// fields[b][ch][i] = mean[ch] + scale[ch] * out[ch][b*hw + i].
-cudaError_t launch_denormalize(const float* out, const float* norm, int batch, int hw,
-                               float* fields, cudaStream_t st);
+// fields[b][ch][i] = mean[ch] + scale[ch] * out[ch][b*hw + i], with the phi channel (ch 3)
+// shifted to the mean cond[b][1] when cond is not null.
+cudaError_t launch_denormalize(const float* out, const float* norm, const float* cond, int batch,
+                               int hw, float* fields, cudaStream_t st);
 // Per-channel FP64 sum and sum of squares of fields [n][4][hw] into partial[4][blocks][2].
 cudaError_t launch_field_moments(const float* fields, int n, int hw, double* partial, int blocks,
                                  cudaStream_t st);

@@ -324,16 +324,30 @@ __global__ void geometry_kernel(float* X, int batch, int ny, int nx) {
   }
 }
 
-__global__ void denormalize_kernel(const float* out, const float* norm, int batch, int hw,
-                                   float* fields) {
-  const int64_t P = (int64_t)batch * hw, n = 4 * P;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int ch = (int)(t / P);
-    const int64_t p = t % P;
-    const int b = (int)(p / hw);
-    const int64_t i = p % hw;
-    fields[((int64_t)b * 4 + ch) * hw + i] = norm[ch] + norm[4 + ch] * out[t];
+// One block per sample: fields[b][ch][i] = mean[ch] + scale[ch] * out[ch][b*hw + i], then the
+// phi channel shifted by a constant so that its mean over the cavity equals the sample's
+// conditioning phi (cond[b][1]): the particle mass of the warm start is the cold start's.
+__global__ void denormalize_kernel(const float* out, const float* norm, const float* cond,
+                                   int batch, int hw, float* fields) {
+  __shared__ double sh[8][1];
+  __shared__ float s_shift;
+  const int b = blockIdx.x;
+  const int64_t P = (int64_t)batch * hw;
+  float shift = 0.f;
+  if (cond) {
+    double acc[1] = {0.0};
+    for (int i = threadIdx.x; i < hw; i += blockDim.x)
+      acc[0] += (double)(norm[3] + norm[7] * out[3 * P + (int64_t)b * hw + i]);
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) s_shift = (float)((double)cond[3 * b + 1] - acc[0] / (double)hw);
+    __syncthreads();
+    shift = s_shift;
+  }
+  for (int ch = 0; ch < 4; ++ch) {
+    const float add = ch == 3 ? shift : 0.f;
+    for (int i = threadIdx.x; i < hw; i += blockDim.x)
+      fields[((int64_t)b * 4 + ch) * hw + i] =
+          norm[ch] + norm[4 + ch] * out[ch * P + (int64_t)b * hw + i] + add;
   }
 }
 
@@ -454,10 +468,9 @@ cudaError_t launch_geometry(float* X, int batch, int ny, int nx, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_denormalize(const float* out, const float* norm, int batch, int hw,
-                               float* fields, cudaStream_t st) {
-  denormalize_kernel<<<grid_for(4LL * batch * hw, 256, 2048), 256, 0, st>>>(out, norm, batch, hw,
-                                                                            fields);
+cudaError_t launch_denormalize(const float* out, const float* norm, const float* cond, int batch,
+                               int hw, float* fields, cudaStream_t st) {
+  denormalize_kernel<<<batch, 256, 0, st>>>(out, norm, cond, batch, hw, fields);
   return cudaGetLastError();
 }
 

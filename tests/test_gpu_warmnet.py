@@ -80,8 +80,11 @@ def test_forward_matches_oracle(ny, nx, c0, hidden):
     net.set_normalizer(mean, scale)
     out = net.forward(torch.from_numpy(CONDS.astype(np.float32))).cpu().numpy()
     cond32 = CONDS.astype(np.float32).astype(np.float64)
-    ref = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, bf16=True)
-    ref64 = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden)
+    phi = cond32[:, 1]
+    ref = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, bf16=True,
+                            phi=phi)
+    ref64 = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, phi=phi)
+    np.testing.assert_allclose(out[:, 3].mean(axis=(1, 2)), phi, rtol=0, atol=1e-6)
     norm = lambda f: (f - mean[None, :, None, None]) / scale[None, :, None, None]  # noqa: E731
     e16, e64 = _rel(norm(out), norm(ref)), _rel(norm(out), norm(ref64))
     print("forward rel L2: vs bf16 oracle %.2e, vs fp64 oracle %.2e" % (e16, e64))
@@ -136,7 +139,8 @@ def test_forward_and_gradient_full_size():
     cond = CONDS[1:2]
     out = net.forward(torch.from_numpy(cond.astype(np.float32))).cpu().numpy()
     c = WN.condition(*cond.astype(np.float32).astype(np.float64).T)
-    ref, _ = WN.forward(p, c, ny, nx, 16, 64, bf16=True)
+    ref = WN.predict_fields(p, c, mean, scale, ny, nx, 16, 64, bf16=True,
+                            phi=cond.astype(np.float32).astype(np.float64)[:, 1])
     assert _rel(out, ref) < 1e-4
     r = np.random.default_rng(12)
     target = r.normal(size=(1, 4, ny, nx)).astype(np.float32)

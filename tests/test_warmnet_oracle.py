@@ -148,3 +148,14 @@ def test_field_stats():
     np.testing.assert_allclose(mean, [7.0] * 4, atol=2.0)
     assert scale[3] == 1.0  # a constant channel keeps unit scale
     np.testing.assert_allclose(mean[:3], [f[:, c].mean() for c in range(3)])
+
+
+def test_predicted_phi_keeps_the_particle_mass():
+    c0, hid, n, p, cond, fields, mean, scale = _tiny()
+    phi = np.array([0.01, 0.04])
+    f = WN.predict_fields(p, cond, mean, scale, n, n, c0, hid, phi=phi)
+    g = WN.predict_fields(p, cond, mean, scale, n, n, c0, hid)
+    np.testing.assert_allclose(f[:, 3].mean(axis=(1, 2)), phi, rtol=1e-13)
+    np.testing.assert_array_equal(f[:, :3], g[:, :3])
+    d = f[:, 3] - g[:, 3]
+    assert np.ptp(d[0]) < 1e-15 and np.ptp(d[1]) < 1e-15  # a constant shift per sample
