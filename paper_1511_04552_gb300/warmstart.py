@@ -199,10 +199,13 @@ def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_eve
     steps = np.zeros(n, dtype=np.int64)
     nu = np.zeros(n)
     fields = torch.empty((n, 4, ny, nx), dtype=torch.float32, device="cuda") if want_fields else None
+    # cavities of similar Ra converge after similar step counts: group them so that a batch does
+    # not run on with a few slow cavities left
+    order = np.argsort(np.asarray(conds, dtype=np.float64)[:, 0], kind="stable")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for g0 in range(0, n, group):
-        idx = range(g0, min(n, g0 + group))
+        idx = [int(i) for i in order[g0:g0 + group]]
         cavs = []
         for i in idx:
             Ra, phi, dp = (float(v) for v in conds[i])

@@ -88,7 +88,12 @@ def test_forward_matches_oracle(ny, nx, c0, hidden):
     norm = lambda f: (f - mean[None, :, None, None]) / scale[None, :, None, None]  # noqa: E731
     e16, e64 = _rel(norm(out), norm(ref)), _rel(norm(out), norm(ref64))
     print("forward rel L2: vs bf16 oracle %.2e, vs fp64 oracle %.2e" % (e16, e64))
-    assert e16 < 1e-4
+    # Against the oracle with the same BF16 operand rounding the residual comes from FP32
+    # accumulation: it perturbs a value by ~sqrt(K) 6e-8 ~ 2e-6 (relative), which flips its
+    # rounding to BF16 with probability ~2e-6 / 2^-8 ~ 5e-4, and a flip moves it by up to
+    # 2^-8; summed over ~10 layers that is ~2e-4 in relative L2. 1e-3 leaves margin; a wrong
+    # index or term is O(1).
+    assert e16 < 1e-3
     assert e64 < 3e-2
 
 
@@ -124,7 +129,9 @@ def test_gradient_matches_oracle_small():
     r = np.random.default_rng(11)
     target = r.normal(size=(3, 4, ny, nx)).astype(np.float32)
     mean, scale = np.array([0.1, 0.0, -0.1, 0.5]), np.array([1.0, 2.0, 0.5, 1.5])
-    _check_grads(net, p, ny, nx, c0, hidden, CONDS, target, mean, scale, 2e-3, 6e-2)
+    # tight bound: the forward pass's rounding-flip noise (see test_forward_matches_oracle)
+    # through twice as many rounded operands (activations, weights, pre-activation gradients)
+    _check_grads(net, p, ny, nx, c0, hidden, CONDS, target, mean, scale, 5e-3, 6e-2)
 
 
 @pytest.mark.slow
@@ -141,10 +148,10 @@ def test_forward_and_gradient_full_size():
     c = WN.condition(*cond.astype(np.float32).astype(np.float64).T)
     ref = WN.predict_fields(p, c, mean, scale, ny, nx, 16, 64, bf16=True,
                             phi=cond.astype(np.float32).astype(np.float64)[:, 1])
-    assert _rel(out, ref) < 1e-4
+    assert _rel(out, ref) < 1e-3
     r = np.random.default_rng(12)
     target = r.normal(size=(1, 4, ny, nx)).astype(np.float32)
-    _check_grads(net, p, ny, nx, 16, 64, cond, target, mean, scale, 2e-3, 6e-2)
+    _check_grads(net, p, ny, nx, 16, 64, cond, target, mean, scale, 5e-3, 6e-2)
 
 
 def test_adam_first_step_and_determinism():
