@@ -104,9 +104,10 @@ int mclbm_net_train_step(mclbm_net_t* net, int batch, const float* cond_dev,
  *   D[z][m][n] = sum over k in split z of A(m, k) B(n, k),   0 <= m < M, 0 <= n < N,
  * A(m, k) = a[m*lda + k] (a_kmajor != 0) or a[k*lda + m]; B(n, k) likewise with b, ldb;
  * BF16 operands, FP32 result d[z*split_stride + m*ldd + n]; K is cut into `splits` ranges of
- * k_per_split (a multiple of 64). Requirements: the contiguous extent of each operand is a
- * multiple of 8 (K for a K-major operand, M or N otherwise), ld* multiples of 8, pointers 16-byte
- * aligned. async on the given stream. */
+ * k_per_split (a multiple of 64), splits * k_per_split >= K. Operands are read with 16-byte
+ * loads where the contiguous extent and the leading dimension are multiples of 8 elements and
+ * the pointer is 16-byte aligned, element by element otherwise. EINVAL for non-positive sizes,
+ * null or odd pointers, or a leading dimension below the contiguous extent. async. */
 int mclbm_gemm_bf16(int M, int N, int K, const void* a, int64_t lda, int a_kmajor, const void* b,
                     int64_t ldb, int b_kmajor, float* d, int64_t ldd, int splits,
                     int64_t k_per_split, int64_t split_stride, void* cuda_stream);

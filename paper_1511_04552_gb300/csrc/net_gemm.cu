@@ -128,11 +128,14 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 }
 
 // Stages rows [r0, r0 + rows) x k [k0, k0 + 64) of an operand; zero outside R x K.
-// K-major: element (r, k) at p[r * ld + k], K % 8 == 0. MN-major: p[k * ld + r], R % 8 == 0.
+// K-major: element (r, k) at p[r * ld + k]; MN-major: p[k * ld + r]. With vec, 16-byte loads
+// (the contiguous extent and ld are multiples of 8 and p is 16-byte aligned); otherwise
+// element loads (small layers whose extents are not multiples of 8).
 __device__ __forceinline__ void stage_operand(uint8_t* dst, const __nv_bfloat16* __restrict__ p,
-                                              int64_t ld, int kmajor, int r0, int rows, int R,
-                                              int64_t k0, int64_t K) {
+                                              int64_t ld, int kmajor, int vec, int r0, int rows,
+                                              int R, int64_t k0, int64_t K) {
   const int tid = threadIdx.x;
+  const uint16_t* p16 = reinterpret_cast<const uint16_t*>(p);
   if (kmajor) {
     // 16-byte chunks: consecutive threads take consecutive rows of one 8-wide k group, so each
     // group of 8 threads writes one contiguous 128-byte core-matrix column (no bank conflicts)
@@ -141,7 +144,16 @@ __device__ __forceinline__ void stage_operand(uint8_t* dst, const __nv_bfloat16*
       const int gr = r0 + r;
       const int64_t gk = k0 + kg * 8;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (gr < R && gk < K) v = __ldg(reinterpret_cast<const uint4*>(p + (int64_t)gr * ld + gk));
+      if (gr < R && gk < K) {
+        if (vec) {
+          v = __ldg(reinterpret_cast<const uint4*>(p + (int64_t)gr * ld + gk));
+        } else {
+          uint16_t* e = reinterpret_cast<uint16_t*>(&v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (gk + j < K) e[j] = __ldg(p16 + (int64_t)gr * ld + gk + j);
+        }
+      }
       *reinterpret_cast<uint4*>(dst + tile_off(r, kg * 8)) = v;
     }
   } else {
@@ -152,8 +164,16 @@ __device__ __forceinline__ void stage_operand(uint8_t* dst, const __nv_bfloat16*
       const int gr = r0 + rc * 8;
       const int64_t gk = k0 + k;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (gr < R && gk < K) v = __ldg(reinterpret_cast<const uint4*>(p + gk * ld + gr));
-      const uint16_t* e = reinterpret_cast<const uint16_t*>(&v);
+      uint16_t* e = reinterpret_cast<uint16_t*>(&v);
+      if (gr < R && gk < K) {
+        if (vec) {
+          v = __ldg(reinterpret_cast<const uint4*>(p + gk * ld + gr));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (gr + j < R) e[j] = __ldg(p16 + gk * ld + gr + j);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         *reinterpret_cast<uint16_t*>(dst + tile_off(rc * 8 + j, k)) = e[j];
@@ -200,8 +220,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(const GemmArgs g) {
       phase[s] ^= 1u;
     }
     const int64_t k0 = kbeg + (int64_t)kb * kBK;
-    stage_operand(sA + s * kStageBytes, g.a, g.lda, g.a_kmajor, m0, kBM, g.M, k0, kend);
-    stage_operand(sB + s * kStageBytes, g.b, g.ldb, g.b_kmajor, n0, n_inst, g.N, k0, kend);
+    stage_operand(sA + s * kStageBytes, g.a, g.lda, g.a_kmajor, g.a_vec, m0, kBM, g.M, k0, kend);
+    stage_operand(sB + s * kStageBytes, g.b, g.ldb, g.b_kmajor, g.b_vec, n0, n_inst, g.N, k0,
+                  kend);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (s_abort) break;
@@ -278,14 +299,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(const GemmArgs g) {
 }  // namespace
 
 bool gemm_args_valid(const GemmArgs& g, int splits) {
-  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || splits <= 0 || splits > 65535) return false;
-  if (!g.a || !g.b || !al16(g.a) || !al16(g.b)) return false;
+  if (!g.a || !g.b) return false;
+  if ((reinterpret_cast<uintptr_t>(g.a) | reinterpret_cast<uintptr_t>(g.b)) & 1u) return false;
   if (g.k_per_split <= 0 || g.k_per_split % kBK) return false;
   if ((int64_t)splits * g.k_per_split < g.K) return false;
-  if (g.lda % 8 || g.ldb % 8) return false;
-  if (g.a_kmajor ? (g.K % 8 || g.lda < g.K) : (g.M % 8 || g.lda < g.M)) return false;
-  if (g.b_kmajor ? (g.K % 8 || g.ldb < g.K) : (g.N % 8 || g.ldb < g.N)) return false;
+  if (g.a_kmajor ? g.lda < g.K : g.lda < g.M) return false;
+  if (g.b_kmajor ? g.ldb < g.K : g.ldb < g.N) return false;
   if (g.mode == kGemmRaw) {
     if (!g.d || g.ldd < g.N) return false;
     if (splits > 1 && g.split_stride < (int64_t)g.M * g.ldd) return false;
@@ -297,8 +317,17 @@ bool gemm_args_valid(const GemmArgs& g, int splits) {
   return true;
 }
 
-cudaError_t launch_gemm(const GemmArgs& g, int splits, cudaStream_t st) {
-  if (!gemm_args_valid(g, splits)) return cudaErrorInvalidValue;
+// 16-byte loads are possible when the contiguous extent and the leading dimension are multiples
+// of 8 elements and the base is 16-byte aligned.
+int vec_ok(const void* p, int64_t ld, int64_t extent) {
+  return ((reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0 && extent % 8 == 0) ? 1 : 0;
+}
+
+cudaError_t launch_gemm(const GemmArgs& g_in, int splits, cudaStream_t st) {
+  if (!gemm_args_valid(g_in, splits)) return cudaErrorInvalidValue;
+  GemmArgs g = g_in;
+  g.a_vec = vec_ok(g.a, g.lda, g.a_kmajor ? g.K : g.M);
+  g.b_vec = vec_ok(g.b, g.ldb, g.b_kmajor ? g.K : g.N);
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;

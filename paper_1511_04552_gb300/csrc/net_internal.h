@@ -33,9 +33,11 @@ struct GemmArgs {
   const __nv_bfloat16* a;
   int64_t lda;
   int a_kmajor;
+  int a_vec;  // set by launch_gemm: 16-byte loads of A
   const __nv_bfloat16* b;
   int64_t ldb;
   int b_kmajor;
+  int b_vec;
   int M, N, K;
   int64_t k_per_split;  // multiple of 64
   float* d;

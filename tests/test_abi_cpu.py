@@ -145,7 +145,13 @@ def test_net_config_and_param_count_match_oracle(pkg):
     assert L.mclbm_net_bind(h, C.c_void_p(256), 16, None) == -1  # too small
     L.mclbm_net_destroy(h)
     # the GEMM validates its operands on the host
-    assert L.mclbm_gemm_bf16(128, 128, 60, C.c_void_p(256), 64, 1, C.c_void_p(256), 64, 1,
-                             C.c_void_p(256), 128, 1, 64, 0, None) == -1  # K % 8 != 0
-    assert L.mclbm_gemm_bf16(12, 128, 64, C.c_void_p(256), 64, 0, C.c_void_p(256), 64, 1,
-                             C.c_void_p(256), 128, 1, 64, 0, None) == -1  # MN-major M % 8 != 0
+    args = lambda **kw: [kw.get(k, v) for k, v in (  # noqa: E731
+        ("M", 128), ("N", 128), ("K", 64), ("a", C.c_void_p(256)), ("lda", 64), ("akm", 1),
+        ("b", C.c_void_p(256)), ("ldb", 64), ("bkm", 1), ("d", C.c_void_p(256)), ("ldd", 128),
+        ("splits", 1), ("kps", 64), ("ss", 0), ("st", None))]
+    assert L.mclbm_gemm_bf16(*args(lda=32)) == -1              # leading dimension below K
+    assert L.mclbm_gemm_bf16(*args(a=C.c_void_p(257))) == -1   # odd address
+    assert L.mclbm_gemm_bf16(*args(kps=96)) == -1              # split not a multiple of 64
+    assert L.mclbm_gemm_bf16(*args(K=200, kps=64, splits=3)) == -1  # splits do not cover K
+    assert L.mclbm_gemm_bf16(*args(M=0)) == -1
+    assert L.mclbm_gemm_bf16(*args(akm=0, lda=100)) == -1      # MN-major: lda below M
