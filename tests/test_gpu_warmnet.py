@@ -109,7 +109,8 @@ def _check_grads(net, p, ny, nx, c0, hidden, cond, target, mean, scale, tight, l
     t64 = target.astype(np.float64)
     l16, g16 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden, bf16=True)
     l64, g64 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden)
-    assert abs(loss - l16) < 1e-5 * l16, (loss, l16)
+    # the loss moves by about twice the output's relative error (bounded by 1e-3 above)
+    assert abs(loss - l16) < 1e-3 * l16, (loss, l16)
     assert abs(loss - l64) < 2e-2 * l64, (loss, l64)
     worst16, worst64 = 0.0, 0.0
     lay, _ = WN.param_layout(c0, hidden)
