@@ -336,26 +336,55 @@ class Cavity:
         return t
 
 
-def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, consecutive=2, max_steps=2_000_000):
-    """Advances until the hot-wall Nusselt number changes by at most tol (relative) between
-    `consecutive` successive checks `check_every` steps apart. Returns a dict with the step
-    count, the final Nusselt numbers, the history and whether the criterion was met."""
+def steady_nu_reached(hist, tol=1e-4, floor=2e-7, spread=0.05):
+    """Steadiness test on the hot-wall Nusselt numbers of successive checks (equal step spacing).
+
+    Steady when the estimated distance to the limit is at most tol * |Nu|: the last five changes
+    d_n, ..., d_(n-4) have one sign and shrink geometrically with a consistent ratio (the four
+    ratios d_k / d_(k-1) lie in [0, 0.99) within `spread` of each other, as on the exponential
+    tail of a relaxation), and the tail of that series, |d_n| r / (1 - r) with the largest ratio,
+    is within tol * |Nu|. A change-below-tolerance test alone also stops where the transient has
+    an extremum, far from the steady value; there the ratios fall quickly instead of staying
+    constant. Also steady when the last two changes are both below floor * |Nu| (the FP32 state
+    has reached its fixed point: changes are round-off and ratios are noise), or when Nu
+    oscillates (two or more sign flips of the change) within half the tolerance over the last
+    six checks."""
+    if len(hist) < 6:
+        return False
+    nu = hist[-1]
+    d = [hist[-k] - hist[-k - 1] for k in range(1, 6)]  # d[0] is the latest change
+    lim = floor * abs(nu)
+    if abs(d[0]) <= lim and abs(d[1]) <= lim:
+        return True
+    # an oscillation about the limit: the sign of the change flips at least twice and the last
+    # six values lie within half the tolerance
+    flips = sum(1 for k in range(4) if d[k] * d[k + 1] < 0.0)
+    if flips >= 2 and max(hist[-6:]) - min(hist[-6:]) <= 0.5 * tol * abs(nu):
+        return True
+    if any(x == 0.0 for x in d[1:]):
+        return False
+    r = [d[k] / d[k + 1] for k in range(4)]
+    if not all(0.0 <= x < 0.99 for x in r) or max(r) - min(r) > spread:
+        return False
+    rm = max(r)
+    return abs(d[0]) * rm / (1.0 - rm) <= tol * abs(nu)
+
+
+def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, max_steps=2_000_000):
+    """Advances until the hot-wall Nusselt number is steady to tol (steady_nu_reached, checks
+    `check_every` steps apart). Returns a dict with the step count, the final Nusselt numbers,
+    the history and whether the criterion was met."""
     hist = []
-    prev = None
-    streak = 0
+    nus = []
     steps = 0
     while steps < max_steps:
         cav.step(check_every)
         steps += check_every
         nh, nc = cav.nusselt()
         hist.append((steps, nh, nc))
-        if prev is not None and abs(nh - prev) <= tol * abs(nh):
-            streak += 1
-            if streak >= consecutive:
-                return dict(steps=steps, nu_hot=nh, nu_cold=nc, history=hist, converged=True)
-        else:
-            streak = 0
-        prev = nh
+        nus.append(nh)
+        if steady_nu_reached(nus, tol):
+            return dict(steps=steps, nu_hot=nh, nu_cold=nc, history=hist, converged=True)
     return dict(steps=steps, nu_hot=hist[-1][1] if hist else None,
                 nu_cold=hist[-1][2] if hist else None, history=hist, converged=False)
 
@@ -422,15 +451,13 @@ class Batch:
             pass
 
 
-def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, consecutive=2,
-                    max_steps=1_000_000):
-    """Runs every cavity of a batch until its hot-wall Nusselt number changes by at most tol
-    (relative) between `consecutive` successive checks; converged cavities leave the tile
-    table. Returns per-cavity step counts and final Nusselt numbers."""
+def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, max_steps=1_000_000):
+    """Runs every cavity of a batch until its hot-wall Nusselt number is steady to tol
+    (steady_nu_reached); converged cavities leave the tile table. Returns per-cavity step
+    counts and final Nusselt numbers."""
     n = len(batch.cavities)
     active = [True] * n
-    streak = [0] * n
-    prev = [None] * n
+    hist = [[] for _ in range(n)]
     done_at = [None] * n
     steps = 0
     nu = np.zeros(n)
@@ -442,20 +469,16 @@ def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, consecutive=2,
         for c in range(n):
             if not active[c]:
                 continue
-            if prev[c] is not None and abs(hot[c] - prev[c]) <= tol * abs(hot[c]):
-                streak[c] += 1
-                if streak[c] >= consecutive:
-                    active[c] = False
-                    done_at[c] = steps
-                    nu[c] = hot[c]
-                    changed = True
-            else:
-                streak[c] = 0
-            prev[c] = hot[c]
+            hist[c].append(hot[c])
+            if steady_nu_reached(hist[c], tol):
+                active[c] = False
+                done_at[c] = steps
+                nu[c] = hot[c]
+                changed = True
         if changed and any(active):
             batch.set_active(active)
     for c in range(n):
         if done_at[c] is None:
-            nu[c] = prev[c]
+            nu[c] = hist[c][-1] if hist[c] else np.nan
     return dict(steps=done_at, nu_hot=nu, total_steps=steps,
                 converged=all(d is not None for d in done_at))

@@ -189,7 +189,7 @@ def sample_conditions(n, seed):
 
 
 def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_every=1000,
-                 consecutive=2, max_steps=2_000_000, want_fields=False, Pr=6.2):
+                 max_steps=2_000_000, want_fields=False, Pr=6.2):
     """Runs every cavity of conds [n][3] to a steady hot-wall Nusselt number with the batched
     solver (groups of `group` cavities per persistent launch). warm: optional device fields
     [n][4][ny][nx] for mclbm_init(WARM). Returns per-cavity steps and Nu, the total wall time
@@ -213,8 +213,7 @@ def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_eve
             cav.init(warm=warm[i] if warm is not None else None)
             cavs.append(cav)
         batch = B.Batch(cavs)
-        res = B.sweep_to_steady(batch, tol=tol, check_every=check_every, consecutive=consecutive,
-                                max_steps=max_steps)
+        res = B.sweep_to_steady(batch, tol=tol, check_every=check_every, max_steps=max_steps)
         for k, i in enumerate(idx):
             steps[i] = res["steps"][k] if res["steps"][k] is not None else res["total_steps"]
             nu[i] = res["nu_hot"][k]

@@ -1,0 +1,58 @@
+"""Host logic of the steady-Nusselt test (binding.steady_nu_reached) on synthetic histories."""
+import numpy as np
+
+from paper_1511_04552_gb300.binding import steady_nu_reached
+
+
+def _first_stop(seq, tol=1e-4):
+    for n in range(1, len(seq) + 1):
+        if steady_nu_reached(list(seq[:n]), tol):
+            return n
+    return None
+
+
+def test_geometric_approach_stops_within_tolerance():
+    """Nu_n = Nu_inf + A r^n from either side: the check stops once the true distance to the
+    limit is at most about tol, never earlier than that by more than the estimate's slack."""
+    for A in (1.0, -0.5, 3.0):
+        for r in (0.5, 0.9, 0.98):
+            seq = 4.0 + A * r ** np.arange(2000)
+            n = _first_stop(seq)
+            assert n is not None
+            dist = abs(seq[n - 1] - 4.0) / 4.0
+            assert dist <= 1.0001e-4, (A, r, dist)
+            assert abs(seq[n - 2] - 4.0) / 4.0 > 0.5e-4 * r  # not long after either
+
+
+def test_extremum_of_the_transient_does_not_stop():
+    """An overshoot: Nu rises, peaks and relaxes; near the peak successive changes are small
+    (a plain change test stops there), but they change sign."""
+    t = np.arange(400) * 1000.0
+    seq = 3.0 - 2.0 * np.exp(-t / 2e4) + 1.5 * (t / 2e4) * np.exp(-t / 2e4)
+    n = _first_stop(seq)
+    assert n is not None
+    peak = int(np.argmax(seq))
+    assert n > peak + 3
+    assert abs(seq[n - 1] - 3.0) <= 1.5e-4 * 3.0
+
+
+def test_damped_oscillation_waits_for_the_floor_or_a_monotone_tail():
+    t = np.arange(3000)
+    seq = 5.0 + 0.1 * np.cos(t * 0.7) * np.exp(-t / 200.0)
+    n = _first_stop(seq)
+    assert n is not None and abs(seq[n - 1] - 5.0) <= 1e-4 * 5.0
+
+
+def test_fixed_point_noise_stops_on_the_floor():
+    r = np.random.default_rng(0)
+    seq = 2.0 + 1e-8 * r.standard_normal(20)
+    assert _first_stop(seq) == 6
+    assert not steady_nu_reached([1.0, 1.1, 1.2, 1.25, 1.27])  # too short
+
+
+def test_small_persistent_wobble_counts_as_steady():
+    """A neutral oscillation of relative amplitude 1e-5 about the limit (e.g. a weakly damped
+    acoustic mode) is steady to 1e-4; one of amplitude 1e-3 is not."""
+    t = np.arange(50)
+    assert _first_stop(3.0 + 3e-5 * np.sin(1.3 * t)) == 6
+    assert _first_stop(3.0 + 3e-3 * np.sin(1.3 * t)) is None
