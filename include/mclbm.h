@@ -65,6 +65,7 @@ extern "C" {
 /* ---- initial states (mclbm_init) --------------------------------------------------------- */
 #define MCLBM_INIT_REST 0 /* rest, uniform phi, theta linear from +1/2 (hot) to -1/2 (cold) */
 #define MCLBM_INIT_WARM 2 /* equilibrium of caller fields [4][ny][nx]: ux, uy, theta, phi */
+#define MCLBM_INIT_WARM_RHO 3 /* ... [5][ny][nx]: ux, uy, theta, phi, rho^w (MCLBM_RHO_W) */
 
 /* ---- storage of the populations (deviations from the initial conduction state) ----------- */
 #define MCLBM_STORE_F32 0  /* 216 bytes per lattice update */
@@ -135,7 +136,11 @@ int mclbm_bind(mclbm_t *h, void *dev_buf, size_t bytes, void *cuda_stream);
 /* Writes the initial populations (equilibria of Eqs 26-27) as the post-collision state of
  * step 0, resets the step counter, the residual snapshot and the sticky divergence flag.
  * mode MCLBM_INIT_REST ignores warm_dev; MCLBM_INIT_WARM reads warm_dev, a device array
- * [4][ny][nx] FP32 of ux, uy, theta and phi (phi in [0, 1)). Async. */
+ * [4][ny][nx] FP32 of ux, uy, theta and phi (phi in [0, 1)), and sets rho^w = 1 - phi;
+ * MCLBM_INIT_WARM_RHO reads [5][ny][nx] with the base-fluid partial density rho^w (the field
+ * MCLBM_RHO_W, normalised by rho_f) as the fifth plane, so that a steady state's pressure field
+ * is part of the warm start (without it the buoyancy is out of balance and the start relaxes
+ * through pressure waves). Async. */
 int mclbm_init(mclbm_t *h, int mode, const float *warm_dev);
 
 /* Advances n >= 0 time steps (Eqs 18-19 with the forces of Table 1 and the walls of

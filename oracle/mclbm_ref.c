@@ -534,25 +534,29 @@ static void collide_node(ref_t *h, const ref_terms *t, int i, int j, double *dst
 
 int mclbm_ref_init(ref_t *h, int mode, const double *warm) {
   if (!h) return REF_EINVAL;
-  if (mode != REF_INIT_REST && mode != REF_INIT_WARM) return REF_EINVAL;
-  if (mode == REF_INIT_WARM && !warm) return REF_EINVAL;
+  if (mode != REF_INIT_REST && mode != REF_INIT_WARM && mode != REF_INIT_WARM_RHO)
+    return REF_EINVAL;
+  if (mode != REF_INIT_REST && !warm) return REF_EINVAL;
   const size_t n = (size_t)h->nx * h->ny;
   double *st = h->st[0];
   for (int j = 0; j < h->ny; ++j)
     for (int i = 0; i < h->nx; ++i) {
-      double ux = 0, uy = 0, th, ph;
+      double ux = 0, uy = 0, th, ph, rw;
       if (mode == REF_INIT_REST) {
         th = 0.5 - (i + 0.5) / h->nx; /* linear conduction profile */
         ph = h->phi0;
+        rw = 1.0 - ph;
       } else {
         const size_t k = (size_t)j * h->nx + i;
         ux = warm[k];
         uy = warm[n + k];
         th = warm[2 * n + k];
         ph = warm[3 * n + k];
+        /* the base-fluid partial density: given (a steady state's pressure field) or 1 - phi */
+        rw = mode == REF_INIT_WARM_RHO ? warm[4 * n + k] : 1.0 - ph;
       }
       double e[NQ];
-      mclbm_ref_equilibrium(1.0 - ph, ux, uy, e);
+      mclbm_ref_equilibrium(rw, ux, uy, e);
       for (int q = 0; q < NQ; ++q) AT(st, q, i, j) = e[q];
       mclbm_ref_equilibrium(ph * h->pr.rho_p / h->pr.rho_f, ux, uy, e);
       for (int q = 0; q < NQ; ++q) AT(st, NQ + q, i, j) = e[q];

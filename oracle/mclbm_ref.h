@@ -45,7 +45,8 @@ extern "C" {
 #define REF_UPY 128u
 
 #define REF_INIT_REST 0
-#define REF_INIT_WARM 2
+#define REF_INIT_WARM 2     /* warm [4][ny][nx]: ux, uy, theta, phi; rho^w = 1 - phi */
+#define REF_INIT_WARM_RHO 3 /* warm [5][ny][nx]: ux, uy, theta, phi, rho^w */
 
 typedef struct {
   double rho_f, cp_f, k_f, beta_f, mu_f; /* base fluid, SI */

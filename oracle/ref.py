@@ -14,7 +14,7 @@ F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127
 UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
-INIT_REST, INIT_WARM = 0, 2
+INIT_REST, INIT_WARM, INIT_WARM_RHO = 0, 2, 3
 
 
 class RefProps(C.Structure):
@@ -170,8 +170,9 @@ class RefSolver:
     def init(self, mode=INIT_REST, warm=None):
         if warm is not None:
             w = np.ascontiguousarray(warm, dtype=np.float64)
-            assert w.shape == (4, self.ny, self.nx)
-            _check(lib().mclbm_ref_init(self._h, INIT_WARM, _dp(w)), "mclbm_ref_init")
+            assert w.shape[1:] == (self.ny, self.nx) and w.shape[0] in (4, 5)
+            _check(lib().mclbm_ref_init(self._h, INIT_WARM if w.shape[0] == 4 else INIT_WARM_RHO,
+                                        _dp(w)), "mclbm_ref_init")
         else:
             _check(lib().mclbm_ref_init(self._h, mode, None), "mclbm_ref_init")
         return self

@@ -16,7 +16,7 @@ F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127
 UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
-INIT_REST, INIT_WARM = 0, 2
+INIT_REST, INIT_WARM, INIT_WARM_RHO = 0, 2, 3
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
 GRAPH_STEPS = 64
@@ -254,12 +254,15 @@ class Cavity:
 
     # -- the C entry points
     def init(self, mode=INIT_REST, warm=None):
-        """mclbm_init. warm: device float32 tensor [4, ny, nx] (ux, uy, theta, phi)."""
+        """mclbm_init. warm: device float32 tensor [4, ny, nx] (ux, uy, theta, phi) or
+        [5, ny, nx] (+ rho^w, mode MCLBM_INIT_WARM_RHO)."""
         if warm is not None:
             assert warm.dtype == self.torch.float32 and warm.is_cuda
-            assert tuple(warm.shape) == (4, self.ny, self.nx) and warm.is_contiguous()
+            assert tuple(warm.shape[1:]) == (self.ny, self.nx) and warm.is_contiguous()
+            assert warm.shape[0] in (4, 5)
             self._warm_keepalive = warm
-            rc = lib().mclbm_init(self._h, INIT_WARM, C.c_void_p(warm.data_ptr()))
+            rc = lib().mclbm_init(self._h, INIT_WARM if warm.shape[0] == 4 else INIT_WARM_RHO,
+                                  C.c_void_p(warm.data_ptr()))
         else:
             rc = lib().mclbm_init(self._h, mode, None)
         self._check(rc, "mclbm_init")

@@ -289,14 +289,14 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
 int mclbm_init(mclbm_t* h, int mode, const float* warm_dev) {
   int rc = ready(h, false);
   if (rc) return rc;
-  if (mode != MCLBM_INIT_REST && mode != MCLBM_INIT_WARM)
+  if (mode != MCLBM_INIT_REST && mode != MCLBM_INIT_WARM && mode != MCLBM_INIT_WARM_RHO)
     return fail(h, MCLBM_EINVAL, "unknown init mode %d", mode);
-  if (mode == MCLBM_INIT_WARM && !warm_dev)
-    return fail(h, MCLBM_EINVAL, "MCLBM_INIT_WARM needs warm fields");
+  if (mode != MCLBM_INIT_REST && !warm_dev)
+    return fail(h, MCLBM_EINVAL, "warm init modes need warm fields");
   h->cur = 0;
   CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
-  CK(h, launch_init(h->state[0], h->L, h->k, mode == MCLBM_INIT_WARM ? warm_dev : nullptr,
-                    h->stream));
+  CK(h, launch_init(h->state[0], h->L, h->k, mode == MCLBM_INIT_REST ? nullptr : warm_dev,
+                    mode == MCLBM_INIT_WARM_RHO ? 1 : 0, h->stream));
   h->steps = 0;
   h->initialised = true;
   h->diverged = false;

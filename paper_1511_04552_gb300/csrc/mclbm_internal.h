@@ -98,8 +98,9 @@ cudaError_t prepare_tma_bf16(StepConfig* c, const Layout& L);
 cudaError_t launch_epoch_advance(uint32_t* epoch, cudaStream_t st);
 cudaError_t launch_stream_only(const void* src, void* dst, const Layout& L, const StepConsts& k,
                                cudaStream_t st);
+// warm: null (rest), [4][ny][nx] (ux, uy, theta, phi) or, with warm_rho, [5][ny][nx] (+ rho^w)
 cudaError_t launch_init(void* dst, const Layout& L, const StepConsts& k, const float* warm,
-                        cudaStream_t st);
+                        int warm_rho, cudaStream_t st);
 cudaError_t launch_fields(const void* src, const Layout& L, const StepConsts& k, uint32_t which,
                           float* out, cudaStream_t st);
 // Nusselt partial sums: red[0] = sum_j (8 T_h - 9 th_0 + th_1) / 3, red[1] = cold-wall twin.

@@ -37,7 +37,7 @@ __global__ void stream_only_kernel(const T* __restrict__ src, T* __restrict__ ds
 // ---- initial equilibrium (Eqs 26-27) ---------------------------------------------------------
 template <class T>
 __global__ void init_kernel(T* __restrict__ dst, const Layout L, const StepConsts k,
-                            const float* __restrict__ warm) {
+                            const float* __restrict__ warm, int warm_rho) {
   const int64_t n = (int64_t)L.nx * L.ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -49,8 +49,9 @@ __global__ void init_kernel(T* __restrict__ dst, const Layout L, const StepConst
       uy = warm[n + t];
       th = warm[2 * n + t];
       const double phi = warm[3 * n + t];
-      // rho^w = 1 - phi, rho^p = phi rho_p / rho_f, as deviations from the initial values
-      drw = (1.0 - phi) - k.rho_w0_d;
+      // rho^w = 1 - phi (or the caller's rho^w field), rho^p = phi rho_f / rho_p, as
+      // deviations from the initial values
+      drw = (warm_rho ? (double)warm[4 * n + t] : 1.0 - phi) - k.rho_w0_d;
       drp = phi / k.fr_d - k.rho_p0_d;
     } else {
       th = 0.5 - ((double)i + 0.5) / (double)L.nx;
@@ -369,11 +370,12 @@ cudaError_t launch_stream_only(const void* src, void* dst, const Layout& L, cons
 }
 
 cudaError_t launch_init(void* dst, const Layout& L, const StepConsts& k, const float* warm,
-                        cudaStream_t st) {
+                        int warm_rho, cudaStream_t st) {
   const int64_t n = (int64_t)L.nx * L.ny;
   return by_storage(L.storage, [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    init_kernel<T><<<grid_for(n, 256, 4096), 256, 0, st>>>(static_cast<T*>(dst), L, k, warm);
+    init_kernel<T><<<grid_for(n, 256, 4096), 256, 0, st>>>(static_cast<T*>(dst), L, k, warm,
+                                                            warm_rho);
     return cudaGetLastError();
   });
 }

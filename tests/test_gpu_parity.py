@@ -237,3 +237,21 @@ def test_step_variants_bitwise_identical(nx, ny, monkeypatch):
         states[name] = cav.state_get()
         cav.nusselt()  # raises MCLBM_ETIMEOUT if a bounded wait gave up
     assert torch.equal(states["tma"], states["tile"])
+
+
+def test_warm_init_with_density_matches_oracle():
+    """MCLBM_INIT_WARM_RHO (ux, uy, theta, phi, rho^w) against the oracle's same init, then 500
+    steps."""
+    import torch
+    nx, ny = 40, 32
+    warm = workloads.perturbed_rest_fields(nx, ny, 0.02, seed=5, amp=1e-3).astype(np.float64)
+    rng = np.random.default_rng(5)
+    rho_w = (1.0 - warm[3]) + 1e-3 * rng.standard_normal((ny, nx))
+    w5 = np.concatenate([warm, rho_w[None]]).astype(np.float32)
+    import paper_1511_04552_gb300 as m
+    import oracle
+    gpu = m.Cavity(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=torch.from_numpy(w5).cuda())
+    ref = oracle.RefSolver(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=w5.astype(np.float64))
+    gpu.step(500)
+    ref.step(500)
+    _assert_parity(gpu, ref)

@@ -430,3 +430,24 @@ def test_saffman_and_magnus_invariants(oracle_mod):
         if np.linalg.norm(FM) > 0:
             seen_magnus_sign.add(np.sign(proj) == np.sign(0.63 - zH))
     assert seen_magnus_sign == {True}
+
+
+def test_warm_init_with_density(oracle_mod):
+    """MCLBM_INIT_WARM_RHO: the fluid populations' zeroth moment is the given rho^w, the
+    particle and thermal sets are those of the 4-field warm start, and rho^w = 1 - phi gives
+    exactly the 4-field state."""
+    import numpy as np
+    ny, nx = 12, 16
+    rng = np.random.default_rng(0)
+    w5 = np.stack([rng.normal(size=(ny, nx)) * 1e-3, rng.normal(size=(ny, nx)) * 1e-3,
+                   rng.normal(size=(ny, nx)) * 0.1, 0.02 + rng.normal(size=(ny, nx)) * 1e-4,
+                   0.98 + rng.normal(size=(ny, nx)) * 1e-3])
+    r5 = oracle_mod.RefSolver(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=w5)
+    r4 = oracle_mod.RefSolver(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=w5[:4])
+    s5, s4 = r5.get_state(), r4.get_state()
+    np.testing.assert_allclose(s5[:9].sum(axis=0), w5[4], rtol=1e-14)
+    np.testing.assert_array_equal(s5[9:], s4[9:])
+    w = w5.copy()
+    w[4] = 1.0 - w[3]
+    r = oracle_mod.RefSolver(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=w)
+    np.testing.assert_array_equal(r.get_state(), s4)
