@@ -1,9 +1,9 @@
 /*
  * mclbm_net.h -- C ABI of the learned warm start in libmclbm.so: a small conditioned
- * convolutional encoder-decoder that predicts the steady fields (u_x, u_y, theta, phi) of a
- * differentially heated cavity from (Ra, phi, d_p), trained and evaluated on the GPU by the
+ * convolutional encoder-decoder that predicts the steady fields (u_x, u_y, theta, phi, rho^w)
+ * of a differentially heated cavity from (Ra, phi, d_p), trained and evaluated on the GPU by the
  * library's own BF16 tensor-core kernels (tcgen05 MMA, FP32 accumulation in tensor memory).
- * Its prediction seeds mclbm_init(MCLBM_INIT_WARM); the plain cold-started solve remains the
+ * Its prediction seeds mclbm_init(MCLBM_INIT_WARM_RHO); the plain cold-started solve remains the
  * judge of the steady state. The paper (arXiv:1511.04552) has no learned component: this is
  * an acceleration of its steady-state computation (the results of its Section 3, e.g. Fig. 8,
  * are steady states), and the network below is this library's own design.
@@ -13,10 +13,12 @@
  *     eta = (j+1/2)/ny - 1/2;  conditioning c = ((log10 Ra - 4.5)/1.5, (phi - 0.025)/0.025,
  *     (d_p/1nm - 55)/45);  conv = 3x3, zero padding 1;  SiLU activations;
  *   e0 = conv(X, 4->C0), e1..e3 = stride-2 convs, e4 = stride-2 conv + FiLM;
- *   d3, d2, d1, d0 = conv(cat(up2(previous), skip)) + FiLM;  out = conv(d0, C0->4);
+ *   d3, d2, d1, d0 = conv(cat(up2(previous), skip)) + FiLM;  out = conv(d0, C0->5);
  *   FiLM: gamma = 1 + r[a:a+C], beta = r[a+C:a+2C], r = W2 silu(W1 c + b1) + b2, slices in the
- *   order e4, d3, d2, d1, d0;  fields = mean + scale * out (per-channel normaliser), the phi
- *   field then shifted to the conditioning phi's mean.
+ *   order e4, d3, d2, d1, d0;  fields = base + mean + scale * out with base = (0, 0, 0, phi,
+ *   1 - phi) (phi and rho^w are learned as deviations from their rest values; per-channel
+ *   normaliser of fields - base), then phi and rho^w shifted so that their cavity means are phi
+ *   and 1 - phi (the solver conserves both components' masses).
  * Parameters: one flat FP32 vector, per conv layer (e0..e4, d3..d0, out) W[Cout][Cin][3][3]
  *   then b[Cout], then W1[hidden][3], b1[hidden], W2[F][hidden], b2[F], F = 2(C4+C3+C2+C1+C0).
  * Every convolution is an im2col GEMM on the tensor cores with BF16 operands (activations,
@@ -28,7 +30,8 @@
  * device memory (one workspace handed over by mclbm_net_bind, plus every input and output) and
  * the stream; calls marked "async" only enqueue work, "syncs" wait for the stream.
  * Layouts: cond [batch][3] FP32 (Ra, phi, d_p in metres) on the device; fields
- * [batch][4][ny][nx] FP32 (u_x, u_y, theta, phi), the layout mclbm_init(WARM) reads.
+ * [batch][5][ny][nx] FP32 (u_x, u_y, theta, phi, rho^w), per sample the layout
+ * mclbm_init(MCLBM_INIT_WARM_RHO) reads and mclbm_fields(UX|UY|THETA|PHI|RHO_W) writes.
  */
 #ifndef MCLBM_NET_H
 #define MCLBM_NET_H
@@ -49,7 +52,7 @@ typedef struct mclbm_net_config {
   int32_t max_batch;  /* largest batch of any call; 1..256, max_batch * ny * nx <= 2^26 */
 } mclbm_net_config;
 
-/* 256 x 256, c0 = 16, hidden = 64, max_batch = 16 (734 148 parameters). */
+/* 256 x 256, c0 = 16, hidden = 64, max_batch = 16 (734 293 parameters). */
 void mclbm_net_config_default(mclbm_net_config* cfg);
 /* Number of FP32 parameters; 0 for an invalid configuration. */
 int64_t mclbm_net_param_count(const mclbm_net_config* cfg);
@@ -77,20 +80,20 @@ int mclbm_net_get_params(mclbm_net_t* net, float* params_dev);
  * identity), biases zero; resets Adam. async. */
 int mclbm_net_init_params(mclbm_net_t* net, uint64_t seed);
 
-/* Per-channel normaliser (host arrays of 4; scale > 0). async. */
-int mclbm_net_set_normalizer(mclbm_net_t* net, const double mean[4], const double scale[4]);
-/* Per-channel mean and standard deviation (scale 1 for a constant channel) of n samples
- * [n][4][ny][nx] on the device, FP64 sums. syncs. */
-int mclbm_net_field_stats(mclbm_net_t* net, int n, const float* fields_dev, double mean[4],
-                          double scale[4]);
+/* Per-channel normaliser of fields - base (host arrays of 5; scale > 0). syncs. */
+int mclbm_net_set_normalizer(mclbm_net_t* net, const double* mean, const double* scale);
+/* Per-channel mean and standard deviation (scale 1 for a constant channel) of fields - base
+ * over n samples (cond [n][3], fields [n][5][ny][nx], both on the device), FP64 sums. mean and
+ * scale: host arrays of 5. syncs. */
+int mclbm_net_field_stats(mclbm_net_t* net, int n, const float* cond_dev, const float* fields_dev,
+                          double* mean, double* scale);
 
-/* Predicted fields [batch][4][ny][nx] for cond [batch][3]: mean + scale * output, and then the
- * phi field shifted by a constant so that its cavity mean is the sample's phi (the warm start
- * carries the particle mass of the cold start). async. */
+/* Predicted fields [batch][5][ny][nx] for cond [batch][3] (see the definition above). async. */
 int mclbm_net_forward(mclbm_net_t* net, int batch, const float* cond_dev, float* fields_dev);
 
-/* Loss (mean squared error of the normalised output against the normalised target fields) and
- * its gradient with respect to the flat parameters (grad_dev, param_count floats). syncs. */
+/* Loss (mean squared error of the normalised output against the normalised target fields
+ * (target - base - mean) / scale, target [batch][5][ny][nx]) and its gradient with respect to
+ * the flat parameters (grad_dev, param_count floats). syncs. */
 int mclbm_net_loss_grad(mclbm_net_t* net, int batch, const float* cond_dev,
                         const float* target_dev, float* grad_dev, double* loss);
 

@@ -1,6 +1,7 @@
 """FP64 CPU restatement of the warm-start network: a conditioned convolutional encoder-decoder
 that maps the cavity parameters (Ra, phi, d_p) and a geometry encoding to the steady fields
-u_x, u_y, theta and phi, used to seed the MCLBM solver.
+u_x, u_y, theta, phi and rho^w (the base-fluid partial density, i.e. the pressure), used to
+seed the MCLBM solver.
 
 TEST INFRASTRUCTURE. Only tests/ (and the smoke check) use this module; the CUDA library never
 imports it and shares no code with it. It is deliberately plain: every convolution is the sum of
@@ -23,16 +24,18 @@ below is the one the CUDA path implements independently:
     d2 = silu(film(conv(cat(up(d3), e2), C3 + C2 -> C2, 1)))
     d1 = silu(film(conv(cat(up(d2), e1), C2 + C1 -> C1, 1)))
     d0 = silu(film(conv(cat(up(d1), e0), C1 + C0 -> C0, 1)))
-    out = conv(d0, C0 -> 4, 1)
+    out = conv(d0, C0 -> 5, 1)
   film(p) = gamma * p + beta per sample and channel, gamma = 1 + r[a : a + C], beta = r[a + C : a + 2C],
   with r = W2 silu(W1 c + b1) + b2 and the FiLM layers e4, d3, d2, d1, d0 taking consecutive
   slices of r in that order.
 * Parameters, one flat FP32 vector: for each conv layer in the order above W [Cout][Cin][3][3]
   then b [Cout]; then W1 [hidden][3], b1 [hidden], W2 [F][hidden], b2 [F], F = 2 (C4+C3+C2+C1+C0).
-* Fields: F_ch = mean_ch + scale_ch * out_ch (per-channel normaliser, not trained); for a
-  warm start the phi field is then shifted by a constant so that its mean over the cavity is
-  the sample's phi (the particle mass is conserved by the solver, so the steady state has it).
-  Loss = mean over samples, channels and nodes of (out - (F_target - mean)/scale)^2.
+* Fields F = (u_x, u_y, theta, phi, rho^w). Channels 3 and 4 are learned as deviations from the
+  sample's rest values, base = (0, 0, 0, phi_0, 1 - phi_0): F_ch = base_ch + mean_ch +
+  scale_ch * out_ch (per-channel normaliser of F - base, not trained). For a warm start phi and
+  rho^w are then shifted by a constant each so that their cavity means are phi_0 and 1 - phi_0:
+  the solver conserves both components' masses, so the steady state has the cold start's.
+  Loss = mean over samples, channels and nodes of (out - (F_target - base - mean)/scale)^2.
 * Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
@@ -44,7 +47,7 @@ accumulation computes; with bf16=False the network is evaluated in plain FP64.
 import numpy as np
 
 N_IN = 4
-N_OUT = 4
+N_OUT = 5
 FILM_LAYERS = ("e4", "d3", "d2", "d1", "d0")
 
 
@@ -188,7 +191,7 @@ def up2_backward(d):
 
 
 def forward(params, cond, ny, nx, c0=16, hidden=64, geom=None, bf16=False):
-    """Network output (normalised fields) [B][4][ny][nx] and the cache for backward().
+    """Network output (normalised fields) [B][5][ny][nx] and the cache for backward().
     cond: [B][3] normalised conditioning (see condition())."""
     P = unpack(np.asarray(params, dtype=np.float64), c0, hidden)
     q = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
@@ -231,7 +234,7 @@ def forward(params, cond, ny, nx, c0=16, hidden=64, geom=None, bf16=False):
 
 
 def backward(params, cache, dout, c0=16, hidden=64, bf16=False):
-    """dL/dparams (flat, FP64) given dL/d(output) [B][4][ny][nx]."""
+    """dL/dparams (flat, FP64) given dL/d(output) [B][5][ny][nx]."""
     P = unpack(np.asarray(params, dtype=np.float64), c0, hidden)
     q = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     grads = {k: np.zeros_like(v) for k, v in P.items()}
@@ -284,16 +287,25 @@ def backward(params, cache, dout, c0=16, hidden=64, bf16=False):
     return pack(grads, c0, hidden)
 
 
-def normalised_target(fields, mean, scale):
-    fields = np.asarray(fields, dtype=np.float64)
+def base_fields(phi):
+    """Per-sample rest values [B][5] of the five fields for volume fractions phi [B]."""
+    phi = np.asarray(phi, dtype=np.float64).reshape(-1)
+    z = np.zeros_like(phi)
+    return np.stack([z, z, z, phi, 1.0 - phi], axis=1)
+
+
+def normalised_target(fields, mean, scale, phi):
+    fields = np.asarray(fields, dtype=np.float64) - base_fields(phi)[:, :, None, None]
     return (fields - np.asarray(mean)[None, :, None, None]) / np.asarray(scale)[None, :, None, None]
 
 
-def loss_and_grad(params, cond, fields, mean, scale, ny, nx, c0=16, hidden=64, bf16=False):
+def loss_and_grad(params, cond, fields, mean, scale, ny, nx, c0=16, hidden=64, bf16=False,
+                  phi=None):
     """Mean squared error of the normalised output against the normalised target fields
-    [B][4][ny][nx], and its gradient with respect to the flat parameters."""
+    [B][5][ny][nx] (phi: the samples' volume fractions, [B]), and its gradient with respect to
+    the flat parameters."""
     out, cache = forward(params, cond, ny, nx, c0, hidden, bf16=bf16)
-    t = normalised_target(fields, mean, scale)
+    t = normalised_target(fields, mean, scale, phi)
     diff = out - t
     loss = float(np.mean(diff * diff))
     dout = 2.0 * diff / diff.size
@@ -301,12 +313,14 @@ def loss_and_grad(params, cond, fields, mean, scale, ny, nx, c0=16, hidden=64, b
 
 
 def predict_fields(params, cond, mean, scale, ny, nx, c0=16, hidden=64, bf16=False, phi=None):
-    """mean + scale * output; with phi (the samples' volume fractions, [B]) the phi channel is
-    then shifted by a constant per sample so that its cavity mean equals phi."""
+    """base + mean + scale * output for the samples' volume fractions phi [B]; phi and rho^w are
+    then shifted by a constant per sample so that their cavity means are phi and 1 - phi."""
     out, _ = forward(params, cond, ny, nx, c0, hidden, bf16=bf16)
-    f = np.asarray(mean)[None, :, None, None] + np.asarray(scale)[None, :, None, None] * out
-    if phi is not None:
-        f[:, 3] += (np.asarray(phi, dtype=np.float64) - f[:, 3].mean(axis=(1, 2)))[:, None, None]
+    base = base_fields(phi)
+    f = (base[:, :, None, None] + np.asarray(mean)[None, :, None, None] +
+         np.asarray(scale)[None, :, None, None] * out)
+    for ch in (3, 4):
+        f[:, ch] += (base[:, ch] - f[:, ch].mean(axis=(1, 2)))[:, None, None]
     return f
 
 
@@ -319,9 +333,10 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def field_stats(fields):
-    """Per-channel mean and standard deviation over samples and nodes: [B][4][ny][nx]."""
-    f = np.asarray(fields, dtype=np.float64)
+def field_stats(fields, phi):
+    """Per-channel mean and standard deviation over samples and nodes of fields - base:
+    [B][5][ny][nx]."""
+    f = np.asarray(fields, dtype=np.float64) - base_fields(phi)[:, :, None, None]
     mean = f.mean(axis=(0, 2, 3))
     std = f.std(axis=(0, 2, 3))
     return mean, np.where(std > 0, std, 1.0)

@@ -145,7 +145,7 @@ def lib():
         L.mclbm_net_set_params.argtypes = [vp, vp]
         L.mclbm_net_get_params.argtypes = [vp, vp]
         L.mclbm_net_set_normalizer.argtypes = [vp, dp, dp]
-        L.mclbm_net_field_stats.argtypes = [vp, C.c_int, vp, dp, dp]
+        L.mclbm_net_field_stats.argtypes = [vp, C.c_int, vp, vp, dp, dp]
         L.mclbm_net_forward.argtypes = [vp, C.c_int, vp, vp]
         L.mclbm_net_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, dp]
         L.mclbm_net_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]

@@ -53,7 +53,7 @@ struct mclbm_net {
   char* ws = nullptr;
   cudaStream_t stream = nullptr;
   float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
-  float* norm = nullptr;  // mean[4], scale[4]
+  float* norm = nullptr;  // mean[5], scale[5] of the fields' deviations from their rest values
   float* X = nullptr;
   float *dcols = nullptr, *wpart = nullptr;
   float *cond_c = nullptr, *a1 = nullptr, *r = nullptr, *dr = nullptr;
@@ -103,7 +103,7 @@ void plan(mclbm_net* n) {
       {C3, C2, C2, 1, 1, 1, 5, 2, 1},  // d2
       {C2, C1, C1, 1, 1, 1, 6, 1, 1},  // d1
       {C1, C0, C0, 1, 1, 1, 7, 0, 1},  // d0
-      {C0, 0, 4, 1, 0, 0, 8, -1, 0},   // out
+      {C0, 0, kFields, 1, 0, 0, 8, -1, 0},  // out
   };
   int64_t off = 0;
   int film_off = 0;
@@ -153,7 +153,7 @@ void plan(mclbm_net* n) {
   size_t bytes = 0;
   const size_t np = (size_t)n->n_params;
   bytes += 4 * align256(np * 4);  // params, grads, adam m, v
-  bytes += align256(8 * 4);       // normaliser
+  bytes += align256(2 * kFields * 4);  // normaliser
   bytes += align256((size_t)4 * B * c.ny * c.nx * 4);  // X
   n->dcols_elems = 0;
   n->wpart_elems = 0;
@@ -172,7 +172,7 @@ void plan(mclbm_net* n) {
   bytes += align256(n->wpart_elems * 4);
   bytes += align256((size_t)B * 3 * 4) + align256((size_t)B * c.hidden * 4) +
            2 * align256((size_t)B * n->F * 4);
-  bytes += align256(kLossBlocks * 8) + align256(8) + align256(4 * kStatBlocks * 2 * 8);
+  bytes += align256(kLossBlocks * 8) + align256(8) + align256(kFields * kStatBlocks * 2 * 8);
   bytes += align256(4);
   n->ws_bytes = bytes;
 }
@@ -193,7 +193,7 @@ void assign(mclbm_net* n) {
   n->grads = carve<float>(p, np);
   n->adam_m = carve<float>(p, np);
   n->adam_v = carve<float>(p, np);
-  n->norm = carve<float>(p, 8);
+  n->norm = carve<float>(p, 2 * kFields);
   n->X = carve<float>(p, (size_t)4 * B * c.ny * c.nx);
   for (int l = 0; l < kNumLayers; ++l) {
     Layer& y = n->L[l];
@@ -214,7 +214,7 @@ void assign(mclbm_net* n) {
   n->dr = carve<float>(p, (size_t)B * n->F);
   n->loss_part = carve<double>(p, kLossBlocks);
   n->loss = carve<double>(p, 1);
-  n->stat_part = carve<double>(p, 4 * kStatBlocks * 2);
+  n->stat_part = carve<double>(p, kFields * kStatBlocks * 2);
   n->err = carve<int>(p, 1);
 }
 
@@ -299,13 +299,14 @@ cudaError_t forward(mclbm_net* n, int batch, const float* cond) {
 }
 
 // Loss and gradients into n->grads (loss into n->loss on the device).
-cudaError_t loss_backward(mclbm_net* n, int batch, const float* target) {
+cudaError_t loss_backward(mclbm_net* n, int batch, const float* cond, const float* target) {
   cudaStream_t st = n->stream;
   const int hw = n->cfg.ny * n->cfg.nx;
   Layer& out = n->L[kNumLayers - 1];
   LossArgs la;
   la.out = out.pre;
   la.target = target;
+  la.cond = cond;
   la.norm = n->norm;
   la.batch = batch;
   la.hw = hw;
@@ -489,7 +490,11 @@ int mclbm_net_bind(mclbm_net_t* n, void* ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(n->adam_m, 0, np, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->adam_v, 0, np, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->err, 0, sizeof(int), st);
-  const float norm[8] = {0.f, 0.f, 0.f, 0.f, 1.f, 1.f, 1.f, 1.f};
+  float norm[2 * kFields];
+  for (int c = 0; c < kFields; ++c) {
+    norm[c] = 0.f;
+    norm[kFields + c] = 1.f;
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(n->norm, norm, sizeof(norm), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = refresh_bf16_weights(n);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -547,15 +552,15 @@ int mclbm_net_get_params(mclbm_net_t* n, float* p) {
   return e == cudaSuccess ? MCLBM_OK : cuda_fail(n, e, "mclbm_net_get_params");
 }
 
-int mclbm_net_set_normalizer(mclbm_net_t* n, const double mean[4], const double scale[4]) {
+int mclbm_net_set_normalizer(mclbm_net_t* n, const double* mean, const double* scale) {
   if (!n || !mean || !scale) return MCLBM_EINVAL;
   if (!n->bound) return fail(n, MCLBM_ESTATE, "mclbm_net: not bound");
-  float v[8];
-  for (int c = 0; c < 4; ++c) {
+  float v[2 * kFields];
+  for (int c = 0; c < kFields; ++c) {
     if (!(scale[c] > 0.0) || !std::isfinite(mean[c]) || !std::isfinite(scale[c]))
       return fail(n, MCLBM_EINVAL, "normaliser channel %d: mean %g scale %g", c, mean[c], scale[c]);
     v[c] = (float)mean[c];
-    v[4 + c] = (float)scale[c];
+    v[kFields + c] = (float)scale[c];
   }
   // the host array must outlive the copy: synchronous on the stream
   cudaError_t e = cudaMemcpyAsync(n->norm, v, sizeof(v), cudaMemcpyHostToDevice, n->stream);
@@ -563,20 +568,21 @@ int mclbm_net_set_normalizer(mclbm_net_t* n, const double mean[4], const double 
   return e == cudaSuccess ? MCLBM_OK : cuda_fail(n, e, "mclbm_net_set_normalizer");
 }
 
-int mclbm_net_field_stats(mclbm_net_t* n, int count, const float* fields, double mean[4],
-                          double scale[4]) {
-  if (!n || !fields || !mean || !scale || count < 1) return MCLBM_EINVAL;
+int mclbm_net_field_stats(mclbm_net_t* n, int count, const float* cond, const float* fields,
+                          double* mean, double* scale) {
+  if (!n || !cond || !fields || !mean || !scale || count < 1) return MCLBM_EINVAL;
   if (!n->bound) return fail(n, MCLBM_ESTATE, "mclbm_net: not bound");
   const int hw = n->cfg.ny * n->cfg.nx;
-  cudaError_t e = launch_field_moments(fields, count, hw, n->stat_part, kStatBlocks, n->stream);
-  std::vector<double> part(4 * kStatBlocks * 2);
+  cudaError_t e =
+      launch_field_moments(fields, cond, count, hw, n->stat_part, kStatBlocks, n->stream);
+  std::vector<double> part(kFields * kStatBlocks * 2);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(part.data(), n->stat_part, part.size() * 8, cudaMemcpyDeviceToHost,
                         n->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
   if (e != cudaSuccess) return cuda_fail(n, e, "mclbm_net_field_stats");
   const double N = (double)count * hw;
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kFields; ++c) {
     double s = 0.0, s2 = 0.0;
     for (int b = 0; b < kStatBlocks; ++b) {
       s += part[(c * kStatBlocks + b) * 2];
@@ -607,7 +613,7 @@ int mclbm_net_loss_grad(mclbm_net_t* n, int batch, const float* cond, const floa
   if (rc != MCLBM_OK) return rc;
   if (!cond || !target || !grad || !loss) return fail(n, MCLBM_EINVAL, "null pointer");
   cudaError_t e = forward(n, batch, cond);
-  if (e == cudaSuccess) e = loss_backward(n, batch, target);
+  if (e == cudaSuccess) e = loss_backward(n, batch, cond, target);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(grad, n->grads, (size_t)n->n_params * 4, cudaMemcpyDeviceToDevice,
                         n->stream);
@@ -621,7 +627,7 @@ int mclbm_net_train_step(mclbm_net_t* n, int batch, const float* cond, const flo
   if (rc != MCLBM_OK) return rc;
   if (!cond || !target || !(lr > 0.f)) return fail(n, MCLBM_EINVAL, "bad argument");
   cudaError_t e = forward(n, batch, cond);
-  if (e == cudaSuccess) e = loss_backward(n, batch, target);
+  if (e == cudaSuccess) e = loss_backward(n, batch, cond, target);
   if (e == cudaSuccess) {
     n->adam_t += 1;
     const double b1 = 0.9, b2 = 0.999;

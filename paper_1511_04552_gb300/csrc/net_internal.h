@@ -11,6 +11,10 @@
 namespace mcl {
 namespace net {
 
+// Predicted fields: u_x, u_y, theta, phi, rho^w. Channels 3 and 4 are learned as deviations from
+// the sample's rest values phi_0 and 1 - phi_0 (base_fields).
+constexpr int kFields = 5;
+
 // Epilogue of the GEMM.
 enum GemmMode : int {
   kGemmRaw = 0,      // D(m, n) -> d[z * split_stride + m * ldd + n]
@@ -118,12 +122,13 @@ cudaError_t launch_mlp_forward(const MlpArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_backward(const MlpArgs& a, const float* dr, float* gW1, float* gb1,
                                 float* gW2, float* gb2, cudaStream_t st);
 
-// Loss against target fields [batch][4][hw]: dout[ch][b*hw + i] = 2 (out - t) / n,
-// t = (F - mean) / scale; per-block FP64 partial sums of (out - t)^2 into partial[blocks].
+// Loss against target fields [batch][5][hw]: dout[ch][b*hw + i] = 2 (out - t) / n,
+// t = (F - base - mean) / scale; per-block FP64 partial sums of (out - t)^2 into partial[blocks].
 struct LossArgs {
-  const float* out;     // [4][batch * hw]
-  const float* target;  // [batch][4][hw]
-  const float* norm;    // mean[4], scale[4]
+  const float* out;     // [5][batch * hw]
+  const float* target;  // [batch][5][hw]
+  const float* cond;    // [batch][3] raw (Ra, phi, d_p): the base of channels 3 and 4
+  const float* norm;    // mean[5], scale[5]
   int batch, hw;
   float* dout;
   double* partial;
@@ -142,13 +147,14 @@ cudaError_t launch_uniform_fill(float* p, int64_t n, float scale, uint64_t seed,
                                 cudaStream_t st);
 // Geometry input X [4][batch * ny * nx].
 cudaError_t launch_geometry(float* X, int batch, int ny, int nx, cudaStream_t st);
-// fields[b][ch][i] = mean[ch] + scale[ch] * out[ch][b*hw + i], with the phi channel (ch 3)
-// shifted to the mean cond[b][1] when cond is not null.
+// fields[b][ch][i] = base[b][ch] + mean[ch] + scale[ch] * out[ch][b*hw + i]; phi (ch 3) and
+// rho^w (ch 4) are then shifted so that their means are phi_0 = cond[b][1] and 1 - phi_0.
 cudaError_t launch_denormalize(const float* out, const float* norm, const float* cond, int batch,
                                int hw, float* fields, cudaStream_t st);
-// Per-channel FP64 sum and sum of squares of fields [n][4][hw] into partial[4][blocks][2].
-cudaError_t launch_field_moments(const float* fields, int n, int hw, double* partial, int blocks,
-                                 cudaStream_t st);
+// Per-channel FP64 sum and sum of squares of fields - base, fields [n][5][hw], cond [n][3], into
+// partial[5][blocks][2].
+cudaError_t launch_field_moments(const float* fields, const float* cond, int n, int hw,
+                                 double* partial, int blocks, cudaStream_t st);
 
 }  // namespace net
 }  // namespace mcl

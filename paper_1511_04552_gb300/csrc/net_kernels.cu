@@ -267,10 +267,16 @@ __global__ void mlp_backward_kernel(const MlpArgs a, const float* dr, float* gW1
 }
 
 // ---- loss -----------------------------------------------------------------------------------
+// Rest value of channel ch for a sample of volume fraction phi0 (phi and rho^w are learned as
+// deviations from phi_0 and 1 - phi_0).
+__device__ __forceinline__ float base_of(int ch, float phi0) {
+  return ch == 3 ? phi0 : (ch == 4 ? 1.f - phi0 : 0.f);
+}
+
 __global__ void loss_kernel(const LossArgs a) {
   __shared__ double sh[8][1];
   const int64_t P = (int64_t)a.batch * a.hw;
-  const int64_t n = 4 * P;
+  const int64_t n = kFields * P;
   const float inv_n2 = (float)(2.0 / (double)n);
   double acc[1] = {0.0};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -279,7 +285,8 @@ __global__ void loss_kernel(const LossArgs a) {
     const int64_t p = t % P;
     const int b = (int)(p / a.hw);
     const int64_t i = p % a.hw;
-    const float tgt = (a.target[((int64_t)b * 4 + ch) * a.hw + i] - a.norm[ch]) / a.norm[4 + ch];
+    const float F = a.target[((int64_t)b * kFields + ch) * a.hw + i];
+    const float tgt = (F - base_of(ch, a.cond[3 * b + 1]) - a.norm[ch]) / a.norm[kFields + ch];
     const float d = a.out[t] - tgt;
     a.dout[t] = inv_n2 * d;
     acc[0] += (double)d * (double)d;
@@ -324,35 +331,40 @@ __global__ void geometry_kernel(float* X, int batch, int ny, int nx) {
   }
 }
 
-// One block per sample: fields[b][ch][i] = mean[ch] + scale[ch] * out[ch][b*hw + i], then the
-// phi channel shifted by a constant so that its mean over the cavity equals the sample's
-// conditioning phi (cond[b][1]): the particle mass of the warm start is the cold start's.
+// One block per sample: fields[b][ch][i] = base + mean[ch] + scale[ch] * out[ch][b*hw + i], then
+// phi and rho^w shifted by a constant each so that their cavity means are phi_0 = cond[b][1] and
+// 1 - phi_0: the warm start carries the cold start's component masses.
 __global__ void denormalize_kernel(const float* out, const float* norm, const float* cond,
                                    int batch, int hw, float* fields) {
-  __shared__ double sh[8][1];
-  __shared__ float s_shift;
+  __shared__ double sh[8][2];
+  __shared__ float s_shift[2];
   const int b = blockIdx.x;
   const int64_t P = (int64_t)batch * hw;
-  float shift = 0.f;
-  if (cond) {
-    double acc[1] = {0.0};
-    for (int i = threadIdx.x; i < hw; i += blockDim.x)
-      acc[0] += (double)(norm[3] + norm[7] * out[3 * P + (int64_t)b * hw + i]);
-    block_sum<1>(acc, sh);
-    if (threadIdx.x == 0) s_shift = (float)((double)cond[3 * b + 1] - acc[0] / (double)hw);
-    __syncthreads();
-    shift = s_shift;
+  const float phi0 = cond[3 * b + 1];
+  double acc[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < hw; i += blockDim.x) {
+    acc[0] += (double)(norm[3] + norm[kFields + 3] * out[3 * P + (int64_t)b * hw + i]);
+    acc[1] += (double)(norm[4] + norm[kFields + 4] * out[4 * P + (int64_t)b * hw + i]);
   }
-  for (int ch = 0; ch < 4; ++ch) {
-    const float add = ch == 3 ? shift : 0.f;
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    // the deviations' means become zero: the fields' means are the rest values
+    s_shift[0] = (float)(-acc[0] / (double)hw);
+    s_shift[1] = (float)(-acc[1] / (double)hw);
+  }
+  __syncthreads();
+  for (int ch = 0; ch < kFields; ++ch) {
+    const float add = ch == 3 ? s_shift[0] : (ch == 4 ? s_shift[1] : 0.f);
+    const float base = base_of(ch, phi0);
     for (int i = threadIdx.x; i < hw; i += blockDim.x)
-      fields[((int64_t)b * 4 + ch) * hw + i] =
-          norm[ch] + norm[4 + ch] * out[ch * P + (int64_t)b * hw + i] + add;
+      fields[((int64_t)b * kFields + ch) * hw + i] =
+          base + ((norm[ch] + norm[kFields + ch] * out[ch * P + (int64_t)b * hw + i]) + add);
   }
 }
 
-// grid (blocks, 4): per channel, block-strided FP64 sums of x and x^2.
-__global__ void field_moments_kernel(const float* fields, int n, int hw, double* partial) {
+// grid (blocks, 5): per channel, block-strided FP64 sums of x - base and (x - base)^2.
+__global__ void field_moments_kernel(const float* fields, const float* cond, int n, int hw,
+                                     double* partial) {
   __shared__ double sh[8][2];
   const int ch = blockIdx.y;
   const int64_t total = (int64_t)n * hw;
@@ -360,7 +372,8 @@ __global__ void field_moments_kernel(const float* fields, int n, int hw, double*
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = t / hw, i = t % hw;
-    const double x = fields[(s * 4 + ch) * hw + i];
+    const double x = (double)fields[(s * kFields + ch) * hw + i] -
+                     (double)base_of(ch, cond[3 * s + 1]);
     acc[0] += x;
     acc[1] += x * x;
   }
@@ -474,9 +487,9 @@ cudaError_t launch_denormalize(const float* out, const float* norm, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_field_moments(const float* fields, int n, int hw, double* partial, int blocks,
-                                 cudaStream_t st) {
-  field_moments_kernel<<<dim3(blocks, 4), 256, 0, st>>>(fields, n, hw, partial);
+cudaError_t launch_field_moments(const float* fields, const float* cond, int n, int hw,
+                                 double* partial, int blocks, cudaStream_t st) {
+  field_moments_kernel<<<dim3(blocks, kFields), 256, 0, st>>>(fields, cond, n, hw, partial);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 """Learned warm start (include/mclbm_net.h): a conditioned convolutional encoder-decoder that
-predicts the steady fields of a cavity from (Ra, phi, d_p), trained on steady solutions that the
-batched MCLBM solver computes, and used to seed mclbm_init(MCLBM_INIT_WARM). The cold-started
-solve stays the judge: a warm-started run must reach the same steady Nusselt number.
+predicts the steady fields (u_x, u_y, theta, phi, rho^w) of a cavity from (Ra, phi, d_p),
+trained on steady solutions that the batched MCLBM solver computes, and used to seed
+mclbm_init(MCLBM_INIT_WARM_RHO). The cold-started solve stays the judge: a warm-started run must
+reach the same steady Nusselt number.
 
 Argument marshalling only: the network's forward, backward and optimiser run in libmclbm's
 kernels; PyTorch holds device memory and picks minibatches.
@@ -17,7 +18,8 @@ import numpy as np
 
 from . import binding as B
 
-N_FIELDS = 4
+N_FIELDS = 5
+FIELD_MASK = B.UX | B.UY | B.THETA | B.PHI | B.RHO_W  # the order of the network's fields
 
 
 class WarmNet:
@@ -82,22 +84,24 @@ class WarmNet:
         return p
 
     def set_normalizer(self, mean, scale):
-        m = (C.c_double * 4)(*[float(v) for v in mean])
-        s = (C.c_double * 4)(*[float(v) for v in scale])
+        m = (C.c_double * N_FIELDS)(*[float(v) for v in mean])
+        s = (C.c_double * N_FIELDS)(*[float(v) for v in scale])
         self._check(B.lib().mclbm_net_set_normalizer(self.handle, m, s), "mclbm_net_set_normalizer")
         self.mean, self.scale = np.array(mean, dtype=float), np.array(scale, dtype=float)
         return self
 
-    def field_stats(self, fields):
-        f = self._dev(fields)
-        m, s = (C.c_double * 4)(), (C.c_double * 4)()
+    def field_stats(self, cond, fields):
+        """Normaliser statistics of fields [n][5][ny][nx] for conditions cond [n][3]."""
+        c, f = self._dev(self.torch.as_tensor(cond)), self._dev(fields)
+        m, s = (C.c_double * N_FIELDS)(), (C.c_double * N_FIELDS)()
         self._check(B.lib().mclbm_net_field_stats(self.handle, int(f.shape[0]),
+                                                  C.c_void_p(c.data_ptr()),
                                                   C.c_void_p(f.data_ptr()), m, s),
                     "mclbm_net_field_stats")
         return np.array(m[:]), np.array(s[:])
 
     def forward(self, cond, out=None):
-        """cond [b][3] (Ra, phi, d_p) -> fields [b][4][ny][nx] on the device."""
+        """cond [b][3] (Ra, phi, d_p) -> fields [b][5][ny][nx] on the device."""
         c = self._dev(self.torch.as_tensor(cond))
         b = int(c.shape[0])
         if out is None:
@@ -192,13 +196,14 @@ def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_eve
                  max_steps=2_000_000, want_fields=False, Pr=6.2):
     """Runs every cavity of conds [n][3] to a steady hot-wall Nusselt number with the batched
     solver (groups of `group` cavities per persistent launch). warm: optional device fields
-    [n][4][ny][nx] for mclbm_init(WARM). Returns per-cavity steps and Nu, the total wall time
-    and, if asked, the steady fields [n][4][ny][nx] (device)."""
+    [n][5][ny][nx] for mclbm_init(WARM_RHO). Returns per-cavity steps and Nu, the total wall
+    time and, if asked, the steady fields [n][5][ny][nx] (device)."""
     import torch
     n = len(conds)
     steps = np.zeros(n, dtype=np.int64)
     nu = np.zeros(n)
-    fields = torch.empty((n, 4, ny, nx), dtype=torch.float32, device="cuda") if want_fields else None
+    fields = (torch.empty((n, N_FIELDS, ny, nx), dtype=torch.float32, device="cuda")
+              if want_fields else None)
     # cavities of similar Ra converge after similar step counts: group them so that a batch does
     # not run on with a few slow cavities left
     order = np.argsort(np.asarray(conds, dtype=np.float64)[:, 0], kind="stable")
@@ -218,7 +223,7 @@ def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_eve
             steps[i] = res["steps"][k] if res["steps"][k] is not None else res["total_steps"]
             nu[i] = res["nu_hot"][k]
             if want_fields:
-                fields[i] = cavs[k].fields(B.UX | B.UY | B.THETA | B.PHI)
+                fields[i] = cavs[k].fields(FIELD_MASK)
         batch.close()
         del cavs
     torch.cuda.synchronize()
@@ -227,11 +232,11 @@ def solve_steady(conds, ny=256, nx=256, warm=None, group=64, tol=1e-4, check_eve
 
 def train(net, conds, fields, epochs=100, batch=16, lr=2e-3, lr_final=1e-4, seed=0, log=None):
     """Adam on random minibatches, learning rate decaying geometrically from lr to lr_final.
-    conds [n][3] (host or device), fields [n][4][ny][nx] (device). Returns the loss history."""
+    conds [n][3] (host or device), fields [n][5][ny][nx] (device). Returns the loss history."""
     import torch
     n = len(conds)
     c_all = torch.as_tensor(np.asarray(conds, dtype=np.float32)).cuda()
-    mean, scale = net.field_stats(fields)
+    mean, scale = net.field_stats(c_all, fields)
     net.set_normalizer(mean, scale)
     g = torch.Generator(device="cpu").manual_seed(int(seed))
     steps_per_epoch = max(1, n // batch)

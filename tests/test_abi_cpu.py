@@ -127,7 +127,7 @@ def test_net_config_and_param_count_match_oracle(pkg):
     cfg = pkg.binding.NetConfig()
     L.mclbm_net_config_default(C.byref(cfg))
     assert (cfg.ny, cfg.nx, cfg.c0, cfg.hidden, cfg.max_batch) == (256, 256, 16, 64, 16)
-    assert L.mclbm_net_param_count(C.byref(cfg)) == WN.param_count(16, 64) == 734148
+    assert L.mclbm_net_param_count(C.byref(cfg)) == WN.param_count(16, 64) == 734293
     for c0, hid in [(8, 16), (24, 5), (64, 1)]:
         c = pkg.binding.NetConfig(32, 48, c0, hid, 2)
         assert L.mclbm_net_param_count(C.byref(c)) == WN.param_count(c0, hid)

@@ -78,7 +78,8 @@ CONDS = np.array([[2.0e3, 0.010, 20e-9], [3.0e5, 0.045, 90e-9], [8.0e4, 0.0, 55e
 def test_forward_matches_oracle(ny, nx, c0, hidden):
     import torch
     net, p = _net(ny, nx, c0, hidden, 3)
-    mean, scale = np.array([0.01, -0.02, 0.1, 0.02]), np.array([0.05, 0.04, 0.3, 0.001])
+    mean = np.array([0.01, -0.02, 0.1, 2e-6, -1e-4])
+    scale = np.array([0.05, 0.04, 0.3, 1e-4, 1e-3])  # FP32 phi resolves 4e-9 absolute
     net.set_normalizer(mean, scale)
     out = net.forward(torch.from_numpy(CONDS.astype(np.float32))).cpu().numpy()
     cond32 = CONDS.astype(np.float32).astype(np.float64)
@@ -86,8 +87,9 @@ def test_forward_matches_oracle(ny, nx, c0, hidden):
     ref = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, bf16=True,
                             phi=phi)
     ref64 = WN.predict_fields(p, WN.condition(*cond32.T), mean, scale, ny, nx, c0, hidden, phi=phi)
-    np.testing.assert_allclose(out[:, 3].mean(axis=(1, 2)), phi, rtol=0, atol=1e-6)
-    norm = lambda f: (f - mean[None, :, None, None]) / scale[None, :, None, None]  # noqa: E731
+    np.testing.assert_allclose(out[:, 3].mean(axis=(1, 2)), phi, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(out[:, 4].mean(axis=(1, 2)), 1.0 - phi, rtol=0, atol=1e-6)
+    norm = lambda f: WN.normalised_target(f, mean, scale, phi)  # noqa: E731
     e16, e64 = _rel(norm(out), norm(ref)), _rel(norm(out), norm(ref64))
     print("forward rel L2: vs bf16 oracle %.2e, vs fp64 oracle %.2e" % (e16, e64))
     # Against the oracle with the same BF16 operand rounding the residual comes from FP32
@@ -107,8 +109,9 @@ def _check_grads(net, p, ny, nx, c0, hidden, cond, target, mean, scale, tight, l
     cond32 = cond.astype(np.float32).astype(np.float64)
     c = WN.condition(*cond32.T)
     t64 = target.astype(np.float64)
-    l16, g16 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden, bf16=True)
-    l64, g64 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden)
+    phi = cond32[:, 1]
+    l16, g16 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden, bf16=True, phi=phi)
+    l64, g64 = WN.loss_and_grad(p, c, t64, mean, scale, ny, nx, c0, hidden, phi=phi)
     # the loss moves by about twice the output's relative error (bounded by 1e-3 above)
     assert abs(loss - l16) < 1e-3 * l16, (loss, l16)
     assert abs(loss - l64) < 2e-2 * l64, (loss, l64)
@@ -130,8 +133,8 @@ def test_gradient_matches_oracle_small():
     c0, hidden = 8, 16
     net, p = _net(ny, nx, c0, hidden, 3, seed=2)
     r = np.random.default_rng(11)
-    target = r.normal(size=(3, 4, ny, nx)).astype(np.float32)
-    mean, scale = np.array([0.1, 0.0, -0.1, 0.5]), np.array([1.0, 2.0, 0.5, 1.5])
+    target = r.normal(size=(3, 5, ny, nx)).astype(np.float32)
+    mean, scale = np.array([0.1, 0.0, -0.1, 0.5, 0.2]), np.array([1.0, 2.0, 0.5, 1.5, 0.8])
     # tight bound: the forward pass's rounding-flip noise (see test_forward_matches_oracle)
     # through twice as many rounded operands (activations, weights, pre-activation gradients)
     _check_grads(net, p, ny, nx, c0, hidden, CONDS, target, mean, scale, 5e-3, 6e-2)
@@ -144,7 +147,7 @@ def test_forward_and_gradient_full_size():
     import torch
     ny = nx = 256
     net, p = _net(ny, nx, 16, 64, 2, seed=3)
-    mean, scale = np.zeros(4), np.ones(4)
+    mean, scale = np.zeros(5), np.ones(5)
     net.set_normalizer(mean, scale)
     cond = CONDS[1:2]
     out = net.forward(torch.from_numpy(cond.astype(np.float32))).cpu().numpy()
@@ -157,7 +160,7 @@ def test_forward_and_gradient_full_size():
     # the rounding-flip noise grows with depth, width and K (K up to 2304 here): 1.9e-3 measured
     assert e16 < 5e-3 and e16 < 0.5 * e64
     r = np.random.default_rng(12)
-    target = r.normal(size=(1, 4, ny, nx)).astype(np.float32)
+    target = r.normal(size=(1, 5, ny, nx)).astype(np.float32)
     _check_grads(net, p, ny, nx, 16, 64, cond, target, mean, scale, 5e-3, 6e-2)
 
 
@@ -169,7 +172,7 @@ def test_adam_first_step_and_determinism():
     c0, hidden = 8, 16
     net, p = _net(ny, nx, c0, hidden, 3, seed=4)
     r = np.random.default_rng(13)
-    target = torch.from_numpy(r.normal(size=(3, 4, ny, nx)).astype(np.float32))
+    target = torch.from_numpy(r.normal(size=(3, 5, ny, nx)).astype(np.float32))
     cond = torch.from_numpy(CONDS.astype(np.float32))
     l1, g1 = net.loss_grad(cond, target)
     l2, g2 = net.loss_grad(cond, target)
@@ -177,8 +180,9 @@ def test_adam_first_step_and_determinism():
     o1 = net.forward(cond).clone()
     assert torch.equal(o1, net.forward(cond))
     c = WN.condition(*CONDS.astype(np.float32).astype(np.float64).T)
-    _, g_ref = WN.loss_and_grad(p, c, target.numpy().astype(np.float64), np.zeros(4), np.ones(4),
-                                ny, nx, c0, hidden, bf16=True)
+    _, g_ref = WN.loss_and_grad(p, c, target.numpy().astype(np.float64), np.zeros(5), np.ones(5),
+                                ny, nx, c0, hidden, bf16=True,
+                                phi=CONDS.astype(np.float32).astype(np.float64)[:, 1])
     lr = 1e-3
     net.train_step(cond, target, lr)
     dp = net.get_params().cpu().numpy().astype(np.float64) - p.astype(np.float32).astype(np.float64)
@@ -195,11 +199,12 @@ def test_training_reduces_loss():
     net = WarmNet(ny, nx, 8, 16, max_batch=2).init_params(5)
     xi = (np.arange(nx) + 0.5) / nx - 0.5
     X, Y = np.meshgrid(xi, xi)
-    f = np.stack([np.stack([np.sin(np.pi * X) * a, np.cos(np.pi * Y) * a, -X * a, X * Y * a])
-                  for a in (1.0, 0.5)]).astype(np.float32)
+    f = np.stack([np.stack([np.sin(np.pi * X) * a, np.cos(np.pi * Y) * a, -X * a,
+                            phi + 1e-5 * X * Y * a, 1.0 - phi + 1e-3 * Y * a])
+                  for a, phi in ((1.0, CONDS[0, 1]), (0.5, CONDS[1, 1]))]).astype(np.float32)
     cond = torch.from_numpy(CONDS[:2].astype(np.float32))
     tgt = torch.from_numpy(f).cuda()
-    net.set_normalizer(*net.field_stats(tgt))
+    net.set_normalizer(*net.field_stats(cond, tgt))
     losses = [net.train_step(cond, tgt, 3e-3) for _ in range(150)]
     print("loss %.3e -> %.3e" % (losses[0], losses[-1]))
     assert losses[-1] < 0.1 * losses[0]

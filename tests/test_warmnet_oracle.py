@@ -51,10 +51,11 @@ def test_upsample_adjoint():
 
 
 def test_param_count_by_hand():
-    # conv weights 685 440, conv biases 612, conditioning MLP 3*64 + 64 + 736*64 + 736 = 48 096
-    assert WN.param_count(16, 64) == 734148
+    # conv weights 685 584 (the 5-channel head has 16*5*9 = 720), conv biases 613, conditioning
+    # MLP 3*64 + 64 + 736*64 + 736 = 48 096
+    assert WN.param_count(16, 64) == 734293
     segs = WN.param_segments(16, 64)
-    assert sum(s for _, s, _ in segs) == 734148
+    assert sum(s for _, s, _ in segs) == 734293
     assert [n for n, _, _ in segs][:2] == ["e0.W", "e0.b"] and segs[-1][0] == "b2"
 
 
@@ -85,9 +86,12 @@ def _tiny(seed=0):
     p = workloads.random_net_params(WN.param_segments(c0, hid), seed=seed).astype(np.float64)
     cond = WN.condition([2e3, 3e5], [0.01, 0.04], [20e-9, 90e-9])
     r = _rng(5 + seed)
-    fields = r.normal(size=(2, 4, n, n))
-    mean, scale = np.array([0.1, -0.2, 0.0, 0.3]), np.array([2.0, 0.5, 1.0, 3.0])
+    fields = r.normal(size=(2, 5, n, n))
+    mean, scale = np.array([0.1, -0.2, 0.0, 0.3, 0.05]), np.array([2.0, 0.5, 1.0, 3.0, 0.7])
     return c0, hid, n, p, cond, fields, mean, scale
+
+
+PHI = np.array([0.01, 0.04])
 
 
 def test_loss_of_constant_output():
@@ -97,12 +101,14 @@ def test_loss_of_constant_output():
     p = np.zeros_like(p)
     lay, _ = WN.param_layout(c0, hid)
     o, _ = lay["out.b"]
-    b = np.array([0.3, -0.1, 0.2, 0.05])
-    p[o:o + 4] = b
-    loss, g = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid)
-    t = (fields - mean[None, :, None, None]) / scale[None, :, None, None]
+    b = np.array([0.3, -0.1, 0.2, 0.05, -0.4])
+    p[o:o + 5] = b
+    loss, g = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid, phi=PHI)
+    base = np.zeros((2, 5))
+    base[:, 3], base[:, 4] = PHI, 1.0 - PHI
+    t = (fields - base[:, :, None, None] - mean[None, :, None, None]) / scale[None, :, None, None]
     assert np.isclose(loss, np.mean((b[None, :, None, None] - t) ** 2), rtol=1e-14)
-    np.testing.assert_allclose(g[o:o + 4], 2.0 * np.mean(b[None, :, None, None] - t, axis=(0, 2, 3)) / 4,
+    np.testing.assert_allclose(g[o:o + 5], 2.0 * np.mean(b[None, :, None, None] - t, axis=(0, 2, 3)) / 5,
                                rtol=1e-12)
 
 
@@ -110,7 +116,7 @@ def test_gradient_matches_central_differences():
     """dL/dp from backward() against (L(p + h e_k) - L(p - h e_k)) / 2h for a few parameters of
     every tensor (FP64, no rounding)."""
     c0, hid, n, p, cond, fields, mean, scale = _tiny()
-    loss, g = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid)
+    loss, g = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid, phi=PHI)
     lay, _ = WN.param_layout(c0, hid)
     r = _rng(9)
     worst = 0.0
@@ -121,8 +127,8 @@ def test_gradient_matches_central_differences():
             pp, pm = p.copy(), p.copy()
             pp[o + k] += h
             pm[o + k] -= h
-            lp = WN.loss_and_grad(pp, cond, fields, mean, scale, n, n, c0, hid)[0]
-            lm = WN.loss_and_grad(pm, cond, fields, mean, scale, n, n, c0, hid)[0]
+            lp = WN.loss_and_grad(pp, cond, fields, mean, scale, n, n, c0, hid, phi=PHI)[0]
+            lm = WN.loss_and_grad(pm, cond, fields, mean, scale, n, n, c0, hid, phi=PHI)[0]
             fd = (lp - lm) / (2 * h)
             err = abs(fd - g[o + k]) / max(abs(fd), 1e-4 * abs(loss))
             worst = max(worst, err)
@@ -134,8 +140,8 @@ def test_bf16_mode_stays_close_to_fp64():
     """Rounding the convolution operands to bfloat16 changes the loss and gradient by about the
     bfloat16 unit roundoff (2^-8), not more."""
     c0, hid, n, p, cond, fields, mean, scale = _tiny(1)
-    l64, g64 = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid)
-    l16, g16 = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid, bf16=True)
+    l64, g64 = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid, phi=PHI)
+    l16, g16 = WN.loss_and_grad(p, cond, fields, mean, scale, n, n, c0, hid, bf16=True, phi=PHI)
     assert abs(l16 - l64) < 2e-2 * l64
     assert np.linalg.norm(g16 - g64) < 5e-2 * np.linalg.norm(g64)
     assert l16 != l64
@@ -143,19 +149,25 @@ def test_bf16_mode_stays_close_to_fp64():
 
 def test_field_stats():
     r = _rng(6)
-    f = r.normal(size=(3, 4, 5, 6)) * np.array([1, 2, 3, 0])[None, :, None, None] + 7.0
-    mean, scale = WN.field_stats(f)
-    np.testing.assert_allclose(mean, [7.0] * 4, atol=2.0)
-    assert scale[3] == 1.0  # a constant channel keeps unit scale
+    phi = np.array([0.0, 0.02, 0.05])
+    f = r.normal(size=(3, 5, 5, 6)) * np.array([1, 2, 3, 0, 1])[None, :, None, None] + 7.0
+    f[:, 3] = phi[:, None, None]  # phi equal to its rest value: a constant deviation
+    mean, scale = WN.field_stats(f, phi)
+    assert scale[3] == 1.0 and mean[3] == 0.0  # a constant channel keeps unit scale
     np.testing.assert_allclose(mean[:3], [f[:, c].mean() for c in range(3)])
+    np.testing.assert_allclose(mean[4], (f[:, 4] - (1.0 - phi)[:, None, None]).mean())
 
 
-def test_predicted_phi_keeps_the_particle_mass():
+def test_predicted_masses_are_the_cold_starts():
+    """phi and rho^w means are phi_0 and 1 - phi_0; the other channels are base + mean +
+    scale * out, and phi, rho^w differ from that by a constant per sample."""
     c0, hid, n, p, cond, fields, mean, scale = _tiny()
-    phi = np.array([0.01, 0.04])
-    f = WN.predict_fields(p, cond, mean, scale, n, n, c0, hid, phi=phi)
-    g = WN.predict_fields(p, cond, mean, scale, n, n, c0, hid)
-    np.testing.assert_allclose(f[:, 3].mean(axis=(1, 2)), phi, rtol=1e-13)
-    np.testing.assert_array_equal(f[:, :3], g[:, :3])
-    d = f[:, 3] - g[:, 3]
-    assert np.ptp(d[0]) < 1e-15 and np.ptp(d[1]) < 1e-15  # a constant shift per sample
+    f = WN.predict_fields(p, cond, mean, scale, n, n, c0, hid, phi=PHI)
+    np.testing.assert_allclose(f[:, 3].mean(axis=(1, 2)), PHI, rtol=1e-13)
+    np.testing.assert_allclose(f[:, 4].mean(axis=(1, 2)), 1.0 - PHI, rtol=1e-13)
+    out, _ = WN.forward(p, cond, n, n, c0, hid)
+    raw = mean[None, :, None, None] + scale[None, :, None, None] * out
+    np.testing.assert_allclose(f[:, :3], raw[:, :3], rtol=1e-14)
+    for ch in (3, 4):
+        d = f[:, ch] - raw[:, ch]
+        assert np.ptp(d[0]) < 1e-14 and np.ptp(d[1]) < 1e-14
