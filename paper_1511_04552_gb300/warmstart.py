@@ -243,6 +243,7 @@ def train(net, conds, fields, epochs=100, batch=16, lr=2e-3, lr_final=1e-4, seed
     total = epochs * steps_per_epoch
     hist = []
     k = 0
+    t0 = time.perf_counter()
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g).cuda()
         acc = 0.0
@@ -253,7 +254,7 @@ def train(net, conds, fields, epochs=100, batch=16, lr=2e-3, lr_final=1e-4, seed
             k += 1
         hist.append(acc / steps_per_epoch)
         if log:
-            log("epoch %d loss %.4e" % (ep, hist[-1]))
+            log("epoch %d loss %.4e (%.1f s)" % (ep, hist[-1], time.perf_counter() - t0))
     return hist
 
 
@@ -283,7 +284,10 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--group", type=int, default=100, help="cavities per batched launch")
-    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--tol", type=float, default=1e-4, help="steady Nu tolerance of the judged solves")
+    ap.add_argument("--data-tol", type=float, default=1e-3,
+                    help="steady Nu tolerance of the training solves (the network's own error is "
+                         "larger than this)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default="warmnet.npz")
     ap.add_argument("--report", default=None, help="JSON file for the evaluation")
@@ -291,7 +295,7 @@ def main(argv=None):
     log = lambda s: print(s, flush=True)  # noqa: E731
     conds = sample_conditions(a.train, a.seed)
     t0 = time.perf_counter()
-    data = solve_steady(conds, a.size, a.size, group=a.group, tol=a.tol, want_fields=True)
+    data = solve_steady(conds, a.size, a.size, group=a.group, tol=a.data_tol, want_fields=True)
     log("generated %d steady solutions in %.1f s (mean %.0f steps)" % (
         a.train, time.perf_counter() - t0, data["steps"].mean()))
     net = WarmNet(a.size, a.size).init_params(a.seed)
