@@ -252,6 +252,15 @@ void mclbm_batch_destroy(mclbm_batch_t *b);
 /* Derived constants of the handle. */
 int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);
 
+/* Checkpoint and resume. mclbm_save writes the current time level exactly as stored (any
+ * storage type), the step count and the stochastic-rounding epoch to a file, with the lattice
+ * size and a fingerprint of the parameters; mclbm_load restores them into a bound handle
+ * created with the same size, storage and parameters (EINVAL for a different lattice or
+ * storage or a file that is not a checkpoint, EPARAM for different parameters), so that the
+ * continued run is bitwise the uninterrupted one. Both sync. */
+int mclbm_save(mclbm_t *h, const char *path);
+int mclbm_load(mclbm_t *h, const char *path);
+
 /* Time steps done since the last mclbm_init or mclbm_state_set (-1 for a NULL handle). */
 int64_t mclbm_steps_done(const mclbm_t *h);
 

@@ -26,7 +26,7 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
            "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
            "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
-           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc",
+           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc", "mclbm_save", "mclbm_load",
            "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
            "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
            "mclbm_batch_last_error", "mclbm_batch_destroy",
@@ -105,6 +105,10 @@ def lib():
         L.mclbm_state_set.argtypes = [vp, vp]
         L.mclbm_run_host.argtypes = [vp, fp, C.c_int64, C.c_uint32, fp, dp, dp]
         L.mclbm_get_consts.argtypes = [vp, C.POINTER(Consts)]
+        L.mclbm_save.argtypes = [vp, C.c_char_p]
+        L.mclbm_load.argtypes = [vp, C.c_char_p]
+        L.mclbm_save.restype = C.c_int
+        L.mclbm_load.restype = C.c_int
         L.mclbm_steps_done.argtypes = [vp]
         L.mclbm_steps_done.restype = C.c_int64
         L.mclbm_last_error.argtypes = [vp]
@@ -284,6 +288,16 @@ class Cavity:
         self._check(lib().mclbm_fields(self._h, int(which), C.c_void_p(out.data_ptr())),
                     "mclbm_fields")
         return out
+
+    def save(self, path):
+        """mclbm_save: checkpoint of the current state (syncs)."""
+        self._check(lib().mclbm_save(self._h, os.fsencode(path)), "mclbm_save")
+        return self
+
+    def load(self, path):
+        """mclbm_load: resume from a checkpoint of a cavity with the same size and parameters."""
+        self._check(lib().mclbm_load(self._h, os.fsencode(path)), "mclbm_load")
+        return self
 
     def nusselt(self):
         a, b = C.c_double(), C.c_double()

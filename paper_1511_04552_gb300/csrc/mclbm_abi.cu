@@ -429,6 +429,117 @@ int mclbm_state_set(mclbm_t* h, const float* dev_in) {
   return snapshot(h);
 }
 
+namespace {
+
+// Checkpoint file: this header, then the current time level's population planes exactly as
+// stored on the device (27 planes of pitch x ny elements of the storage type).
+struct CheckpointHeader {
+  char magic[8];  // "MCLBMCK1"
+  uint32_t version;
+  int32_t nx, ny, pitch, storage, rounding;
+  int64_t steps;
+  uint32_t epoch, reserved;
+  double Ra, Pr, phi, d_p;
+  uint64_t props_hash;
+  uint64_t payload_bytes;
+};
+
+void fnv1a(uint64_t& x, const void* v, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(v);
+  for (size_t i = 0; i < n; ++i) {
+    x ^= b[i];
+    x *= 1099511628211ull;
+  }
+}
+
+// FNV-1a over the properties' values, field by field (no padding bytes)
+uint64_t props_hash(const mclbm_props& p) {
+  uint64_t x = 1469598103934665603ull;
+  const double d[14] = {p.rho_f, p.cp_f, p.k_f,  p.beta_f, p.mu_f, p.rho_p, p.cp_p,
+                        p.k_p,   p.beta_p, p.T0_K, p.dT_K,   p.g,    p.l_f,  p.Ma};
+  fnv1a(x, d, sizeof(d));
+  fnv1a(x, &p.force_mask, sizeof(p.force_mask));
+  fnv1a(x, &p.storage, sizeof(p.storage));
+  fnv1a(x, &p.rounding, sizeof(p.rounding));
+  return x;
+}
+
+size_t level_bytes(const mclbm_t* h) { return (size_t)kPlanes * h->L.plane * h->L.elem; }
+
+}  // namespace
+
+int mclbm_save(mclbm_t* h, const char* path) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!path) return fail(h, MCLBM_EINVAL, "NULL path");
+  CheckpointHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "MCLBMCK1", 8);
+  hd.version = 1;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.pitch = h->L.pitch;
+  hd.storage = h->props.storage;
+  hd.rounding = h->props.rounding;
+  hd.steps = h->steps;
+  hd.Ra = h->Ra;
+  hd.Pr = h->Pr;
+  hd.phi = h->phi;
+  hd.d_p = h->d_p;
+  hd.props_hash = props_hash(h->props);
+  hd.payload_bytes = level_bytes(h);
+  std::vector<char> buf(hd.payload_bytes);
+  CK(h, cudaMemcpyAsync(&hd.epoch, h->epoch, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(buf.data(), h->state[h->cur], buf.size(), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, MCLBM_EINVAL, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                  std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(h, MCLBM_EINVAL, "writing %s failed", path);
+  return MCLBM_OK;
+}
+
+int mclbm_load(mclbm_t* h, const char* path) {
+  int rc = ready(h, false);
+  if (rc) return rc;
+  if (!path) return fail(h, MCLBM_EINVAL, "NULL path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, MCLBM_EINVAL, "cannot open %s", path);
+  CheckpointHeader hd;
+  std::vector<char> buf;
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, "MCLBMCK1", 8) == 0 &&
+            hd.version == 1;
+  if (ok && (hd.nx != h->nx || hd.ny != h->ny || hd.pitch != h->L.pitch ||
+             hd.storage != h->props.storage || hd.payload_bytes != level_bytes(h))) {
+    std::fclose(f);
+    return fail(h, MCLBM_EINVAL, "%s: lattice or storage differs from the handle's", path);
+  }
+  if (ok && (hd.Ra != h->Ra || hd.Pr != h->Pr || hd.phi != h->phi || hd.d_p != h->d_p ||
+             hd.props_hash != props_hash(h->props))) {
+    std::fclose(f);
+    return fail(h, MCLBM_EPARAM, "%s: parameters differ from the handle's", path);
+  }
+  if (ok) {
+    buf.resize(hd.payload_bytes);
+    ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+  }
+  std::fclose(f);
+  if (!ok) return fail(h, MCLBM_EINVAL, "%s is not a checkpoint of this library", path);
+  h->cur = 0;
+  CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+  CK(h, cudaMemcpyAsync(h->state[0], buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(h->epoch, &hd.epoch, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));  // the host buffers go out of scope
+  h->steps = hd.steps;
+  h->initialised = true;
+  h->diverged = false;
+  return snapshot(h);
+}
+
 int mclbm_run_host(mclbm_t* h, const float* warm_host, int64_t n, uint32_t which,
                    float* fields_host, double* nu_hot, double* nu_cold) {
   int rc = ready(h, false);

@@ -255,3 +255,30 @@ def test_warm_init_with_density_matches_oracle():
     gpu.step(500)
     ref.step(500)
     _assert_parity(gpu, ref)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_checkpoint_resume_is_bitwise(storage, tmp_path):
+    """save after 300 steps, run 200 more; a fresh handle loads the file and runs 200: the same
+    state bit for bit (stochastic rounding included) and the same step count."""
+    import torch
+    import paper_1511_04552_gb300 as m
+    st = {"f32": m.STORE_F32, "bf16": m.STORE_BF16}[storage]
+    a = m.Cavity(70, 50, 1e5, 6.2, 0.03, 30e-9, storage=st).init()
+    a.step(300)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(200)
+    b = m.Cavity(70, 50, 1e5, 6.2, 0.03, 30e-9, storage=st).load(path)
+    assert b.steps_done() == 300
+    b.step(200)
+    assert torch.equal(a.state_get(), b.state_get())
+    assert a.nusselt() == b.nusselt()
+    c = m.Cavity(70, 50, 2e5, 6.2, 0.03, 30e-9, storage=st)
+    with pytest.raises(m.MclbmError) as e:
+        c.load(path)
+    assert e.value.code == m.binding.EPARAM
+    d = m.Cavity(72, 50, 1e5, 6.2, 0.03, 30e-9, storage=st)
+    with pytest.raises(m.MclbmError) as e:
+        d.load(path)
+    assert e.value.code == m.binding.EINVAL
