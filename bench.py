@@ -251,7 +251,7 @@ def sweep_measure(m, torch, steps=1000, tune_steps=64):
 WARMNET = os.path.join(ROOT, "paper_1511_04552_gb300", "weights", "warmnet_256.npz")
 
 
-def warm_start_measure(m, torch, n_points=20):
+def warm_start_measure(m, torch, n_points=12):
     """Learned warm start against cold starts on held-out parameter points (256^2, steady Nu to
     1e-4): both sides solved with the batched solver; the warm side's wall time includes the
     network's inference."""
@@ -389,7 +389,7 @@ def main():
         sc = m.Cavity(w2["nx"], w2["ny"], w2["Ra"], w2["Pr"], w2["phi"], w2["d_p"]).init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = m.run_to_steady(sc, tol=1e-4, check_every=1000, max_steps=1000000)
+        res = m.run_to_steady(sc, tol=1e-4, check_every=1000, max_steps=3000000)
         extras["steady_nu"] = {"wall_s": time.perf_counter() - t0, "steps": res["steps"],
                                "converged": res["converged"], "nu_hot": res["nu_hot"],
                                "nu_cold": res["nu_cold"], "workload": w2["name"]}

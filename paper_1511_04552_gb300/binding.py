@@ -353,30 +353,17 @@ class Cavity:
         return t
 
 
-def steady_nu_reached(hist, tol=1e-4, floor=2e-7, spread=0.05):
-    """Steadiness test on the hot-wall Nusselt numbers of successive checks (equal step spacing).
-
-    Steady when the estimated distance to the limit is at most tol * |Nu|: the last five changes
-    d_n, ..., d_(n-4) have one sign and shrink geometrically with a consistent ratio (the four
-    ratios d_k / d_(k-1) lie in [0, 0.99) within `spread` of each other, as on the exponential
-    tail of a relaxation), and the tail of that series, |d_n| r / (1 - r) with the largest ratio,
-    is within tol * |Nu|. A change-below-tolerance test alone also stops where the transient has
-    an extremum, far from the steady value; there the ratios fall quickly instead of staying
-    constant. Also steady when the last two changes are both below floor * |Nu| (the FP32 state
-    has reached its fixed point: changes are round-off and ratios are noise), or when Nu
-    oscillates (two or more sign flips of the change) within half the tolerance over the last
-    six checks."""
-    if len(hist) < 6:
-        return False
-    nu = hist[-1]
-    d = [hist[-k] - hist[-k - 1] for k in range(1, 6)]  # d[0] is the latest change
+def _geometric_tail_ok(pts, tol, floor, spread):
+    """pts: six values, latest first, equally spaced. See steady_nu_reached."""
+    nu = pts[0]
+    d = [pts[k] - pts[k + 1] for k in range(5)]  # d[0] is the latest change
     lim = floor * abs(nu)
     if abs(d[0]) <= lim and abs(d[1]) <= lim:
         return True
-    # an oscillation about the limit: the sign of the change flips at least twice and the last
-    # six values lie within half the tolerance
+    # an oscillation about the limit: the sign of the change flips at least twice and the six
+    # values lie within half the tolerance
     flips = sum(1 for k in range(4) if d[k] * d[k + 1] < 0.0)
-    if flips >= 2 and max(hist[-6:]) - min(hist[-6:]) <= 0.5 * tol * abs(nu):
+    if flips >= 2 and max(pts) - min(pts) <= 0.5 * tol * abs(nu):
         return True
     if any(x == 0.0 for x in d[1:]):
         return False
@@ -387,7 +374,35 @@ def steady_nu_reached(hist, tol=1e-4, floor=2e-7, spread=0.05):
     return abs(d[0]) * rm / (1.0 - rm) <= tol * abs(nu)
 
 
-def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, max_steps=2_000_000):
+STRICT_LAGS = (1, 32)
+
+
+def steady_nu_reached(hist, tol=1e-4, lags=STRICT_LAGS, floor=2e-7, spread=0.05):
+    """Steadiness test on the hot-wall Nusselt numbers of successive checks (equal step spacing).
+
+    For every lag L in `lags` (in checks), the six values Nu_n, Nu_(n-L), ..., Nu_(n-5L) must
+    pass: the five changes have one sign and shrink geometrically with a consistent ratio (four
+    ratios in [0, 0.99) within `spread` of each other, as on the exponential tail of a
+    relaxation) and the tail of that series, |d_n| r / (1 - r) with the largest ratio, is within
+    tol * |Nu|; or the last two changes are below floor * L * |Nu| (the FP32 state at its fixed
+    point: changes are round-off); or Nu oscillates (two or more sign flips) within half the
+    tolerance. A change-below-tolerance test alone also stops where the transient has an
+    extremum. One lag alone is fooled where a faster mode dominates the short-lag changes while a
+    slow one (here the particle component's migration, over 1e5-1e6 steps) still moves Nu: on
+    256^2 cavities, lag 1 alone stopped up to 1.7e-3 away from the Nu reached 1.5 M steps later,
+    lags (1, 32) at most 8.4e-5."""
+    need = 5 * max(lags) + 1
+    if len(hist) < need:
+        return False
+    for L in lags:
+        pts = [hist[-1 - k * L] for k in range(6)]
+        if not _geometric_tail_ok(pts, tol, floor * L, spread):
+            return False
+    return True
+
+
+def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, max_steps=3_000_000,
+                  lags=STRICT_LAGS):
     """Advances until the hot-wall Nusselt number is steady to tol (steady_nu_reached, checks
     `check_every` steps apart). Returns a dict with the step count, the final Nusselt numbers,
     the history and whether the criterion was met."""
@@ -400,7 +415,7 @@ def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, max_steps=2_000_000):
         nh, nc = cav.nusselt()
         hist.append((steps, nh, nc))
         nus.append(nh)
-        if steady_nu_reached(nus, tol):
+        if steady_nu_reached(nus, tol, lags):
             return dict(steps=steps, nu_hot=nh, nu_cold=nc, history=hist, converged=True)
     return dict(steps=steps, nu_hot=hist[-1][1] if hist else None,
                 nu_cold=hist[-1][2] if hist else None, history=hist, converged=False)
@@ -468,7 +483,8 @@ class Batch:
             pass
 
 
-def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, max_steps=1_000_000):
+def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, max_steps=3_000_000,
+                    lags=STRICT_LAGS):
     """Runs every cavity of a batch until its hot-wall Nusselt number is steady to tol
     (steady_nu_reached); converged cavities leave the tile table. Returns per-cavity step
     counts and final Nusselt numbers."""
@@ -487,7 +503,7 @@ def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, max_steps=1_000_00
             if not active[c]:
                 continue
             hist[c].append(hot[c])
-            if steady_nu_reached(hist[c], tol):
+            if steady_nu_reached(hist[c], tol, lags):
                 active[c] = False
                 done_at[c] = steps
                 nu[c] = hot[c]

@@ -4,9 +4,9 @@ import numpy as np
 from paper_1511_04552_gb300.binding import steady_nu_reached
 
 
-def _first_stop(seq, tol=1e-4):
+def _first_stop(seq, tol=1e-4, lags=(1, 32)):
     for n in range(1, len(seq) + 1):
-        if steady_nu_reached(list(seq[:n]), tol):
+        if steady_nu_reached(list(seq[:n]), tol, lags):
             return n
     return None
 
@@ -21,7 +21,8 @@ def test_geometric_approach_stops_within_tolerance():
             assert n is not None
             dist = abs(seq[n - 1] - 4.0) / 4.0
             assert dist <= 1.0001e-4, (A, r, dist)
-            assert abs(seq[n - 2] - 4.0) / 4.0 > 0.5e-4 * r  # not long after either
+            if n > 161:  # not long after either (161 checks: the history the lags need)
+                assert abs(seq[n - 2] - 4.0) / 4.0 > 0.5e-4 * r
 
 
 def test_extremum_of_the_transient_does_not_stop():
@@ -45,14 +46,24 @@ def test_damped_oscillation_waits_for_the_floor_or_a_monotone_tail():
 
 def test_fixed_point_noise_stops_on_the_floor():
     r = np.random.default_rng(0)
-    seq = 2.0 + 1e-8 * r.standard_normal(20)
-    assert _first_stop(seq) == 6
-    assert not steady_nu_reached([1.0, 1.1, 1.2, 1.25, 1.27])  # too short
+    seq = 2.0 + 1e-8 * r.standard_normal(400)
+    assert _first_stop(seq) == 161  # the first six values 32 checks apart
+    assert _first_stop(seq, lags=(1,)) == 6
+    assert not steady_nu_reached([1.0, 1.1, 1.2, 1.25, 1.27], lags=(1,))  # too short
 
 
 def test_small_persistent_wobble_counts_as_steady():
     """A neutral oscillation of relative amplitude 1e-5 about the limit (e.g. a weakly damped
     acoustic mode) is steady to 1e-4; one of amplitude 1e-3 is not."""
-    t = np.arange(50)
-    assert _first_stop(3.0 + 3e-5 * np.sin(1.3 * t)) == 6
+    t = np.arange(400)
+    assert _first_stop(3.0 + 3e-5 * np.sin(1.3 * t)) == 161
     assert _first_stop(3.0 + 3e-3 * np.sin(1.3 * t)) is None
+
+
+def test_slow_mode_behind_a_fast_one():
+    """Nu = 3 + 0.5 e^(-t/3) + 2e-3 e^(-t/300) (checks as time unit): the two-lag test stops
+    within the tolerance of the limit."""
+    t = np.arange(6000)
+    seq = 3.0 + 0.5 * np.exp(-t / 3.0) + 2e-3 * np.exp(-t / 300.0)
+    n = _first_stop(seq)
+    assert n is not None and abs(seq[n - 1] - 3.0) <= 1e-4 * 3.0
