@@ -292,19 +292,30 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default="warmnet.npz")
     ap.add_argument("--report", default=None, help="JSON file for the evaluation")
+    ap.add_argument("--init", default=None, help="start from these weights (a saved network)")
+    ap.add_argument("--data-strict", action="store_true",
+                    help="training solves to the judged steadiness (both lags, --tol): targets at "
+                         "the end of each cold path instead of a point on it")
+    ap.add_argument("--lr", type=float, default=2e-3)
     a = ap.parse_args(argv)
     log = lambda s: print(s, flush=True)  # noqa: E731
     conds = sample_conditions(a.train, a.seed)
     t0 = time.perf_counter()
     # training targets: points on each cold path near its quasi-steady state (one lag, looser
     # tolerance); a warm start that reproduces such a point follows the cold path from there
-    data = solve_steady(conds, a.size, a.size, group=a.group, tol=a.data_tol, want_fields=True,
-                        lags=(1,))
+    if a.data_strict:
+        data = solve_steady(conds, a.size, a.size, group=a.group, tol=a.tol, want_fields=True)
+    else:
+        data = solve_steady(conds, a.size, a.size, group=a.group, tol=a.data_tol,
+                            want_fields=True, lags=(1,))
     log("generated %d steady solutions in %.1f s (mean %.0f steps)" % (
         a.train, time.perf_counter() - t0, data["steps"].mean()))
-    net = WarmNet(a.size, a.size).init_params(a.seed)
+    if a.init:
+        net = WarmNet.load(a.init)
+    else:
+        net = WarmNet(a.size, a.size).init_params(a.seed)
     t0 = time.perf_counter()
-    hist = train(net, conds, data["fields"], epochs=a.epochs, log=log)
+    hist = train(net, conds, data["fields"], epochs=a.epochs, lr=a.lr, log=log)
     log("trained %d epochs in %.1f s, final loss %.3e" % (a.epochs, time.perf_counter() - t0,
                                                           hist[-1]))
     net.save(a.out)
@@ -312,6 +323,8 @@ def main(argv=None):
     ev = evaluate(net, held, group=a.group, tol=a.tol, ny=a.size, nx=a.size)
     summary = {k: (v.tolist() if isinstance(v, np.ndarray) else v) for k, v in ev.items()}
     summary["train_loss"] = hist
+    summary["train_steps_mean"] = float(data["steps"].mean())
+    summary["train_gen_s"] = data["wall_s"]
     log(json.dumps({k: summary[k] for k in ("n", "cold_wall_s", "warm_wall_s", "speedup_wall",
                                             "speedup_steps")}))
     if a.report:
