@@ -182,6 +182,41 @@ def gemm_bf16(a, b, a_kmajor=True, b_kmajor=True, splits=1, k_per_split=None, st
     return d
 
 
+def conv_flops(ny=256, nx=256, c0=16, batch=1):
+    """Multiply-add FLOPs (2 per MAC) of the network's convolutions for one forward pass of a
+    batch (the backward pass does twice as many: input and weight gradients)."""
+    C = (c0, 2 * c0, 4 * c0, 8 * c0, 8 * c0)
+    # (cin, cout, output grid divisor) per layer, in the order of include/mclbm_net.h
+    layers = [(4, C[0], 1), (C[0], C[1], 2), (C[1], C[2], 4), (C[2], C[3], 8), (C[3], C[4], 16),
+              (C[4] + C[3], C[3], 8), (C[3] + C[2], C[2], 4), (C[2] + C[1], C[1], 2),
+              (C[1] + C[0], C[0], 1), (C[0], N_FIELDS, 1)]
+    return sum(2.0 * batch * (ny // s) * (nx // s) * co * 9 * ci for ci, co, s in layers)
+
+
+def bench_train(steps=20, batch=16, ny=256, nx=256, seed=0):
+    """Times training steps of the network on synthetic targets (CUDA events on the bound
+    stream): ms per step and the convolution FLOP rate (forward + backward = 3x forward)."""
+    import torch
+    net = WarmNet(ny, nx, max_batch=batch).init_params(seed)
+    r = np.random.default_rng(seed)
+    cond = torch.as_tensor(sample_conditions(batch, seed).astype(np.float32)).cuda()
+    tgt = torch.as_tensor(r.standard_normal((batch, N_FIELDS, ny, nx)).astype(np.float32)).cuda()
+    net.set_normalizer(*net.field_stats(cond, tgt))
+    for _ in range(3):
+        net.train_step(cond, tgt, 1e-4, want_loss=False)
+    st = net.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        net.train_step(cond, tgt, 1e-4, want_loss=False)
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    flops = 3.0 * conv_flops(ny, nx, net.cfg.c0, batch)
+    return {"ms_per_step": ms, "batch": batch, "conv_tflops_per_s": flops / (ms * 1e-3) / 1e12,
+            "conv_gflop_per_step": flops / 1e9}
+
+
 # ---- data, training and evaluation drivers ----------------------------------------------------
 
 def sample_conditions(n, seed):
@@ -297,8 +332,13 @@ def main(argv=None):
                     help="training solves to the judged steadiness (both lags, --tol): targets at "
                          "the end of each cold path instead of a point on it")
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--bench-train", type=int, default=0,
+                    help="only time this many training steps on synthetic targets and exit")
     a = ap.parse_args(argv)
     log = lambda s: print(s, flush=True)  # noqa: E731
+    if a.bench_train:
+        log(json.dumps(bench_train(a.bench_train, ny=a.size, nx=a.size)))
+        return
     conds = sample_conditions(a.train, a.seed)
     t0 = time.perf_counter()
     # training targets: points on each cold path near its quasi-steady state (one lag, looser

@@ -40,7 +40,7 @@ def test_trained_network_shortens_the_steady_solve():
 def test_warm_start_from_exact_steady_fields():
     """The mechanism without the network: seeding a cavity with its own steady (u, theta, phi,
     rho^w) must return to the same steady Nu within the steadiness tolerance, faster than the
-    cold start; without rho^w (MCLBM_INIT_WARM) the pressure field is missing."""
+    cold start."""
     import paper_1511_04552_gb300 as m
     from paper_1511_04552_gb300.warmstart import FIELD_MASK
     Ra, phi, dp = 3e4, 0.02, 40e-9
