@@ -25,7 +25,7 @@ def test_trained_network_shortens_the_steady_solve():
     """Four held-out points at 256^2: the warm starts need fewer steps in total than the cold
     starts and reach the same steady Nu within the model's path dependence (the particle
     component's slow migration keeps an imperfect start's Nu a few 1e-4 from the cold path's;
-    measured over 100 points: median 1.4e-4, max 5.6e-4)."""
+    measured over 100 points with the shipped network: median 2.8e-4, max 8.2e-4)."""
     from paper_1511_04552_gb300 import warmstart as W
     assert os.path.exists(WEIGHTS), "the trained network must ship with the package"
     net = W.WarmNet.load(WEIGHTS)
