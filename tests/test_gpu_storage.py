@@ -74,3 +74,26 @@ def test_accuracy_against_fp64_oracle(storage, nu_tol, u_tol, th_tol):
     mw, mp = cav.mass()
     rw, rp = ref.mass()
     assert abs(mw - rw) <= 1e-4 * rw and abs(mp - rp) <= 1e-3 * rp
+
+
+@pytest.mark.parametrize("storage,nu_tol", [("f16", 5e-3), ("bf16", 3e-2)])
+def test_per_result_error_at_1024(storage, nu_tol):
+    """The precision configuration: 1024^2, Ra 1e6, phi 2 %, 50 nm, 20 000 steps from rest. The
+    reference is the FP32-storage run (within 1e-5 of the FP64 oracle by the parity tests; the
+    oracle itself would need hours here). Errors per result: mean hot-wall Nu, max |u|, and the
+    relative L2 of the concentration's deviation from its initial value."""
+    import paper_1511_04552_gb300 as m
+    w = workloads.CAVITY_1024
+    ref = m.Cavity(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"]).init().step(20000)
+    cav = _cav(w["nx"], w["ny"], w["Ra"], w["phi"], w["d_p"], storage).init().step(20000)
+    fr, fc = ref.fields(m.UX | m.UY | m.PHI), cav.fields(m.UX | m.UY | m.PHI)
+    nu_r, nu_c = ref.nusselt()[0], cav.nusselt()[0]
+    umax_r = float((fr[0] ** 2 + fr[1] ** 2).sqrt().max())
+    umax_c = float((fc[0] ** 2 + fc[1] ** 2).sqrt().max())
+    dphi_r, dphi_c = (fr[2] - w["phi"]).double(), (fc[2] - w["phi"]).double()
+    e_nu = abs(nu_c - nu_r) / nu_r
+    e_u = abs(umax_c - umax_r) / umax_r
+    e_phi = float((dphi_c - dphi_r).norm() / dphi_r.norm())
+    print("%s at 1024^2: Nu %.2e, max|u| %.2e, phi deviation L2 %.2e" % (storage, e_nu, e_u, e_phi))
+    assert e_nu <= nu_tol
+    assert e_u <= 10 * nu_tol
