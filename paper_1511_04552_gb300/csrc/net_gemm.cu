@@ -6,7 +6,8 @@
 //  * all threads stage 128 x 64 slices of A and B in shared memory in the canonical K-major
 //    no-swizzle layout of the tensor cores (8-row x 16-byte core matrices: core matrices
 //    adjacent along K are 128 B apart, 8-row groups 1024 B apart), from K-major or MN-major
-//    global operands; two stages, so the next slice is staged while the MMAs read the other;
+//    global operands, each thread issuing all 16 of its 16-byte loads before storing; two
+//    stages, so the next slice is staged while the MMAs read the other;
 //  * one thread issues four tcgen05.mma.kind::f16 (M 128, N up to 128, K 16) per slice with
 //    the FP32 accumulator in tensor memory (128 columns allocated per CTA) and commits them to
 //    the stage's mbarrier;
@@ -127,53 +128,73 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
   return (uint32_t)((((r >> 3) * 8 + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
-// Stages rows [r0, r0 + rows) x k [k0, k0 + 64) of an operand; zero outside R x K.
-// K-major: element (r, k) at p[r * ld + k]; MN-major: p[k * ld + r]. With vec, 16-byte loads
-// (the contiguous extent and ld are multiples of 8 and p is 16-byte aligned); otherwise
-// element loads (small layers whose extents are not multiples of 8).
-__device__ __forceinline__ void stage_operand(uint8_t* dst, const __nv_bfloat16* __restrict__ p,
-                                              int64_t ld, int kmajor, int vec, int r0, int rows,
-                                              int R, int64_t k0, int64_t K) {
+// Staging of rows [r0, r0 + rows) x k [k0, k0 + 64) of an operand (rows <= 128), zero outside
+// R x K, in two phases so that each thread has all of its (at most 8) 16-byte global loads in
+// flight before the first shared-memory store: load_operand into registers, store_operand into
+// the canonical layout. K-major: element (r, k) at p[r * ld + k]; MN-major: p[k * ld + r]. With
+// vec, 16-byte loads (the contiguous extent and ld are multiples of 8 and p is 16-byte
+// aligned); otherwise element loads (small layers whose extents are not multiples of 8).
+// K-major items: consecutive threads take consecutive rows of one 8-wide k group, so each group
+// of 8 threads stores one contiguous 128-byte core-matrix column (no bank conflicts). MN-major
+// items: consecutive threads read consecutive 8-row chunks of one k (coalesced).
+constexpr int kStageItems = 8;  // 16-byte items per thread: 128 x 64 BF16 / (128 x 8)
+
+__device__ __forceinline__ void load_operand(uint4 (&v)[kStageItems],
+                                             const __nv_bfloat16* __restrict__ p, int64_t ld,
+                                             int kmajor, int vec, int r0, int rows, int R,
+                                             int64_t k0, int64_t K) {
   const int tid = threadIdx.x;
   const uint16_t* p16 = reinterpret_cast<const uint16_t*>(p);
-  if (kmajor) {
-    // 16-byte chunks: consecutive threads take consecutive rows of one 8-wide k group, so each
-    // group of 8 threads writes one contiguous 128-byte core-matrix column (no bank conflicts)
-    for (int it = tid; it < rows * 8; it += blockDim.x) {
-      const int r = it % rows, kg = it / rows;
-      const int gr = r0 + r;
-      const int64_t gk = k0 + kg * 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  const int total = rows * 8;  // = (rows / 8) * 64 for the MN-major items as well
+#pragma unroll
+  for (int u = 0; u < kStageItems; ++u) {
+    const int it = tid + u * 128;
+    v[u] = make_uint4(0u, 0u, 0u, 0u);
+    if (it >= total) continue;
+    uint16_t* e = reinterpret_cast<uint16_t*>(&v[u]);
+    if (kmajor) {
+      const int gr = r0 + it % rows;
+      const int64_t gk = k0 + (it / rows) * 8;
       if (gr < R && gk < K) {
         if (vec) {
-          v = __ldg(reinterpret_cast<const uint4*>(p + (int64_t)gr * ld + gk));
+          v[u] = __ldg(reinterpret_cast<const uint4*>(p + (int64_t)gr * ld + gk));
         } else {
-          uint16_t* e = reinterpret_cast<uint16_t*>(&v);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (gk + j < K) e[j] = __ldg(p16 + (int64_t)gr * ld + gk + j);
         }
       }
-      *reinterpret_cast<uint4*>(dst + tile_off(r, kg * 8)) = v;
-    }
-  } else {
-    // 16-byte chunks along the rows: consecutive threads read consecutive 8-row chunks of one k
-    const int chunks = rows / 8;
-    for (int it = tid; it < chunks * kBK; it += blockDim.x) {
-      const int rc = it % chunks, k = it / chunks;
-      const int gr = r0 + rc * 8;
-      const int64_t gk = k0 + k;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      uint16_t* e = reinterpret_cast<uint16_t*>(&v);
+    } else {
+      const int chunks = rows / 8;
+      const int gr = r0 + (it % chunks) * 8;
+      const int64_t gk = k0 + it / chunks;
       if (gr < R && gk < K) {
         if (vec) {
-          v = __ldg(reinterpret_cast<const uint4*>(p + gk * ld + gr));
+          v[u] = __ldg(reinterpret_cast<const uint4*>(p + gk * ld + gr));
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (gr + j < R) e[j] = __ldg(p16 + gk * ld + gr + j);
         }
       }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_operand(uint8_t* dst, const uint4 (&v)[kStageItems],
+                                              int kmajor, int rows) {
+  const int tid = threadIdx.x;
+  const int total = rows * 8;
+#pragma unroll
+  for (int u = 0; u < kStageItems; ++u) {
+    const int it = tid + u * 128;
+    if (it >= total) continue;
+    if (kmajor) {
+      *reinterpret_cast<uint4*>(dst + tile_off(it % rows, (it / rows) * 8)) = v[u];
+    } else {
+      const int chunks = rows / 8;
+      const int rc = it % chunks, k = it / chunks;
+      const uint16_t* e = reinterpret_cast<const uint16_t*>(&v[u]);
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         *reinterpret_cast<uint16_t*>(dst + tile_off(rc * 8 + j, k)) = e[j];
@@ -220,9 +241,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(const GemmArgs g) {
       phase[s] ^= 1u;
     }
     const int64_t k0 = kbeg + (int64_t)kb * kBK;
-    stage_operand(sA + s * kStageBytes, g.a, g.lda, g.a_kmajor, g.a_vec, m0, kBM, g.M, k0, kend);
-    stage_operand(sB + s * kStageBytes, g.b, g.ldb, g.b_kmajor, g.b_vec, n0, n_inst, g.N, k0,
-                  kend);
+    {
+      uint4 va[kStageItems], vb[kStageItems];
+      load_operand(va, g.a, g.lda, g.a_kmajor, g.a_vec, m0, kBM, g.M, k0, kend);
+      load_operand(vb, g.b, g.ldb, g.b_kmajor, g.b_vec, n0, n_inst, g.N, k0, kend);
+      store_operand(sA + s * kStageBytes, va, g.a_kmajor, kBM);
+      store_operand(sB + s * kStageBytes, vb, g.b_kmajor, n_inst);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (s_abort) break;
