@@ -360,7 +360,8 @@ cudaError_t loss_backward(mclbm_net* n, int batch, const float* cond, const floa
                                   n->grads + y.w_off, st)) != cudaSuccess)
       return e;
     if (l == 0) break;
-    // input gradient: dcols[p][k] = sum_o dpre[o][p] wb[o][k]
+    // input gradient: dcols[k][p] = sum_o dpre[o][p] wb[o][k], stored column-major so that
+    // the epilogue's stores and col2im's reads are coalesced over pixels
     std::memset(&g, 0, sizeof(g));
     g.a = y.dpre;
     g.lda = P;
@@ -373,7 +374,8 @@ cudaError_t loss_backward(mclbm_net* n, int batch, const float* cond, const floa
     g.K = y.cout;
     g.k_per_split = ((y.cout + 63) / 64) * 64;
     g.d = n->dcols;
-    g.ldd = y.Kp;
+    g.ldd = P;
+    g.d_trans = 1;
     g.mode = kGemmRaw;
     g.err = n->err;
     if ((e = launch_gemm(g, 1, st)) != cudaSuccess) return e;

@@ -292,10 +292,18 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(const GemmArgs g) {
       }
       if (row >= g.M) continue;
       if (g.mode == kGemmRaw) {
-        float* dst = g.d + (int64_t)blockIdx.z * g.split_stride + (int64_t)row * g.ldd + n0 + c0;
+        float* d = g.d + (int64_t)blockIdx.z * g.split_stride;
+        if (g.d_trans) {
+          // column-major: for each column the warp's 32 rows are 32 consecutive floats
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (n0 + c0 + j < g.N) dst[j] = v[j];
+          for (int j = 0; j < 16; ++j)
+            if (n0 + c0 + j < g.N) d[(int64_t)(n0 + c0 + j) * g.ldd + row] = v[j];
+        } else {
+          float* dst = d + (int64_t)row * g.ldd + n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n0 + c0 + j < g.N) dst[j] = v[j];
+        }
       } else {
         const ConvEpilogue& e = g.ep;
         const int b = row / e.hw;
@@ -332,8 +340,8 @@ bool gemm_args_valid(const GemmArgs& g, int splits) {
   if (g.a_kmajor ? g.lda < g.K : g.lda < g.M) return false;
   if (g.b_kmajor ? g.ldb < g.K : g.ldb < g.N) return false;
   if (g.mode == kGemmRaw) {
-    if (!g.d || g.ldd < g.N) return false;
-    if (splits > 1 && g.split_stride < (int64_t)g.M * g.ldd) return false;
+    if (!g.d || g.ldd < (g.d_trans ? g.M : g.N)) return false;
+    if (splits > 1 && g.split_stride < (int64_t)(g.d_trans ? g.N : g.M) * g.ldd) return false;
   } else if (g.mode == kGemmConvFwd) {
     if (splits != 1 || !g.ep.bias || !g.ep.pre || g.ep.hw <= 0 || g.M % g.ep.hw) return false;
   } else {

@@ -17,7 +17,7 @@ constexpr int kFields = 5;
 
 // Epilogue of the GEMM.
 enum GemmMode : int {
-  kGemmRaw = 0,      // D(m, n) -> d[z * split_stride + m * ldd + n]
+  kGemmRaw = 0,      // D(m, n) -> d[z * split_stride + m * ldd + n] (d_trans: + n * ldd + m)
   kGemmConvFwd = 1,  // m = pixel p, n = output channel o (see ConvEpilogue)
 };
 
@@ -46,6 +46,7 @@ struct GemmArgs {
   int64_t k_per_split;  // multiple of 64
   float* d;
   int64_t ldd, split_stride;
+  int d_trans;  // raw epilogue stores D column-major (coalesced when N is small and M large)
   int mode;
   ConvEpilogue ep;
   int* err;  // bit 0 set when a bounded wait gave up (may be null)
@@ -68,7 +69,8 @@ struct Im2colArgs {
 };
 cudaError_t launch_im2col(const Im2colArgs& a, cudaStream_t st);
 
-// Gradient with respect to one source of a convolution's input from dcols [P][Kp] (FP32):
+// Gradient with respect to one source of a convolution's input from dcols [Kp][P] (FP32,
+// column k = c * 9 + tap of the im2col matrix stored contiguously over the P output pixels):
 // channels [c_lo, c_lo + C) of the concatenated input, source grid Hs x Ws (H/2 if up).
 struct Col2imArgs {
   const float* dcols;

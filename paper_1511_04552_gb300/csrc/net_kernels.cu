@@ -91,6 +91,7 @@ __global__ void im2col_kernel(const Im2colArgs a) {
 __global__ void col2im_kernel(const Col2imArgs a) {
   const int Hs = a.up ? a.H / 2 : a.H, Ws = a.up ? a.W / 2 : a.W;
   const int64_t n = (int64_t)a.C * a.batch * Hs * Ws;
+  const int64_t P = (int64_t)a.batch * a.Ho * a.Wo;  // rows of dcols' columns
   const int rep = a.up ? 2 : 1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -117,7 +118,7 @@ __global__ void col2im_kernel(const Col2imArgs a) {
             const int xo = nxx / a.stride;
             if (xo >= a.Wo) continue;
             const int64_t p = ((int64_t)b * a.Ho + yo) * a.Wo + xo;
-            sum += a.dcols[p * a.Kp + cin * 9 + ky * 3 + kx];
+            sum += a.dcols[(int64_t)(cin * 9 + ky * 3 + kx) * P + p];
           }
         }
       }
