@@ -139,6 +139,13 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 // items: consecutive threads read consecutive 8-row chunks of one k (coalesced).
 constexpr int kStageItems = 8;  // 16-byte items per thread: 128 x 64 BF16 / (128 x 8)
 
+// MN-major item `it` (8 rows at one k): a warp covers 2 row chunks x 16 consecutive k, so
+// pairs of threads read adjacent 16-byte pieces of one 32-byte sector and the 2-byte stores of
+// a warp hit each bank at most 4 times (consecutive row chunks on one k would all hit the same
+// bank: the layout puts 8-row groups 1024 bytes apart).
+__device__ __forceinline__ int mn_chunk(int it) { return (it & 1) + 2 * (it >> 7); }
+__device__ __forceinline__ int mn_k(int it) { return (it >> 1) & 63; }
+
 __device__ __forceinline__ void load_operand(uint4 (&v)[kStageItems],
                                              const __nv_bfloat16* __restrict__ p, int64_t ld,
                                              int kmajor, int vec, int r0, int rows, int R,
@@ -165,9 +172,9 @@ __device__ __forceinline__ void load_operand(uint4 (&v)[kStageItems],
         }
       }
     } else {
-      const int chunks = rows / 8;
-      const int gr = r0 + (it % chunks) * 8;
-      const int64_t gk = k0 + it / chunks;
+      const int rc = mn_chunk(it), kk = mn_k(it);
+      const int gr = r0 + rc * 8;
+      const int64_t gk = k0 + kk;
       if (gr < R && gk < K) {
         if (vec) {
           v[u] = __ldg(reinterpret_cast<const uint4*>(p + gk * ld + gr));
@@ -181,8 +188,10 @@ __device__ __forceinline__ void load_operand(uint4 (&v)[kStageItems],
   }
 }
 
+// Rows at or beyond R are not stored: they only feed rows (A) or columns (B) of D that the
+// epilogue discards, so whatever the stage buffer holds there is harmless.
 __device__ __forceinline__ void store_operand(uint8_t* dst, const uint4 (&v)[kStageItems],
-                                              int kmajor, int rows) {
+                                              int kmajor, int r0, int rows, int R) {
   const int tid = threadIdx.x;
   const int total = rows * 8;
 #pragma unroll
@@ -190,10 +199,12 @@ __device__ __forceinline__ void store_operand(uint8_t* dst, const uint4 (&v)[kSt
     const int it = tid + u * 128;
     if (it >= total) continue;
     if (kmajor) {
-      *reinterpret_cast<uint4*>(dst + tile_off(it % rows, (it / rows) * 8)) = v[u];
+      const int r = it % rows;
+      if (r0 + r >= R) continue;
+      *reinterpret_cast<uint4*>(dst + tile_off(r, (it / rows) * 8)) = v[u];
     } else {
-      const int chunks = rows / 8;
-      const int rc = it % chunks, k = it / chunks;
+      const int rc = mn_chunk(it), k = mn_k(it);
+      if (r0 + rc * 8 >= R) continue;
       const uint16_t* e = reinterpret_cast<const uint16_t*>(&v[u]);
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -245,8 +256,8 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(const GemmArgs g) {
       uint4 va[kStageItems], vb[kStageItems];
       load_operand(va, g.a, g.lda, g.a_kmajor, g.a_vec, m0, kBM, g.M, k0, kend);
       load_operand(vb, g.b, g.ldb, g.b_kmajor, g.b_vec, n0, n_inst, g.N, k0, kend);
-      store_operand(sA + s * kStageBytes, va, g.a_kmajor, kBM);
-      store_operand(sB + s * kStageBytes, vb, g.b_kmajor, n_inst);
+      store_operand(sA + s * kStageBytes, va, g.a_kmajor, m0, kBM, g.M);
+      store_operand(sB + s * kStageBytes, vb, g.b_kmajor, n0, n_inst, g.N);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
