@@ -266,14 +266,14 @@ WARMNET = os.path.join(ROOT, "paper_1511_04552_gb300", "weights", "warmnet_256.n
 
 def warm_start_measure(m, torch, n_points=12):
     """Learned warm start against cold starts on held-out parameter points (256^2, steady Nu to
-    1e-4): both sides solved with the batched solver; the warm side's wall time includes the
-    network's inference."""
+    1e-4): warm and cold solved with the batched solver (the warm side's wall time includes the
+    network's inference), and the plain method: each point solved cold on its own."""
     if not os.path.exists(WARMNET):
         return {"unavailable": "no trained network weights in the package"}
     from paper_1511_04552_gb300 import warmstart as W
     net = W.WarmNet.load(WARMNET)
     conds = workloads.random_conditions(n_points, seed=2)
-    ev = W.evaluate(net, conds, group=n_points)
+    ev = W.evaluate(net, conds, group=n_points, plain=True)
     return {"workload": "%d held-out points, 256^2, log-uniform Ra 1e3..1e6, phi 0..5 %%, "
                         "d_p 10..100 nm" % n_points,
             "cold_wall_s": ev["cold_wall_s"], "warm_wall_s": ev["warm_wall_s"],
@@ -281,7 +281,11 @@ def warm_start_measure(m, torch, n_points=12):
             "cold_steps_mean": float(ev["cold_steps"].mean()),
             "warm_steps_mean": float(ev["warm_steps"].mean()),
             "max_nu_rel_diff": float(ev["nu_rel_diff"].max()),
-            "inference_s": ev["inference_s"]}
+            "inference_s": ev["inference_s"],
+            # the same points solved cold one by one with each cavity's own launches
+            "plain_wall_s": ev["plain_wall_s"],
+            "speedup_vs_plain": ev["speedup_vs_plain"],
+            "max_nu_rel_diff_vs_plain": float(ev["nu_rel_diff_plain"].max())}
 
 
 def time_steps_only(cav, torch, nsteps):

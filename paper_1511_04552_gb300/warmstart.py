@@ -294,9 +294,27 @@ def train(net, conds, fields, epochs=100, batch=16, lr=2e-3, lr_final=1e-4, seed
     return hist
 
 
-def evaluate(net, conds, group=64, tol=1e-4, ny=256, nx=256):
-    """Cold against warm-started steady solves of the same points: steps, wall time (the warm
-    side includes the network's inference) and the steady Nusselt numbers."""
+def solve_plain(conds, ny=256, nx=256, tol=1e-4, Pr=6.2):
+    """Each point solved cold on its own (one cavity's launches, run_to_steady), one after
+    another: the plain method without batching or a learned start."""
+    import torch
+    steps, nu = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in conds:
+        Ra, phi, dp = (float(v) for v in c)
+        r = B.run_to_steady(B.Cavity(nx, ny, Ra, Pr, phi, dp).init(), tol=tol)
+        steps.append(r["steps"])
+        nu.append(r["nu_hot"])
+    torch.cuda.synchronize()
+    return dict(steps=np.array(steps), nu=np.array(nu), wall_s=time.perf_counter() - t0)
+
+
+def evaluate(net, conds, group=64, tol=1e-4, ny=256, nx=256, plain=False):
+    """Cold against warm-started steady solves of the same points, both batched: steps, wall time
+    (the warm side includes the network's inference) and the steady Nusselt numbers. With plain,
+    also each point solved cold on its own, one after another (solve_plain), and the speedup of
+    the warm-started batched sweep over those plain solves."""
     import torch
     cold = solve_steady(conds, ny, nx, group=group, tol=tol)
     torch.cuda.synchronize()
@@ -306,11 +324,17 @@ def evaluate(net, conds, group=64, tol=1e-4, ny=256, nx=256):
     t_inf = time.perf_counter() - t0
     warm = solve_steady(conds, ny, nx, warm=pred, group=group, tol=tol)
     rel = np.abs(warm["nu"] - cold["nu"]) / np.abs(cold["nu"])
-    return dict(n=len(conds), cold_steps=cold["steps"], warm_steps=warm["steps"],
-                cold_wall_s=cold["wall_s"], warm_wall_s=warm["wall_s"] + t_inf,
-                inference_s=t_inf, nu_cold=cold["nu"], nu_warm=warm["nu"], nu_rel_diff=rel,
-                speedup_wall=cold["wall_s"] / (warm["wall_s"] + t_inf),
-                speedup_steps=float(cold["steps"].sum()) / float(warm["steps"].sum()))
+    out = dict(n=len(conds), cold_steps=cold["steps"], warm_steps=warm["steps"],
+               cold_wall_s=cold["wall_s"], warm_wall_s=warm["wall_s"] + t_inf,
+               inference_s=t_inf, nu_cold=cold["nu"], nu_warm=warm["nu"], nu_rel_diff=rel,
+               speedup_wall=cold["wall_s"] / (warm["wall_s"] + t_inf),
+               speedup_steps=float(cold["steps"].sum()) / float(warm["steps"].sum()))
+    if plain:
+        pl = solve_plain(conds, ny, nx, tol=tol)
+        out.update(plain_steps=pl["steps"], plain_wall_s=pl["wall_s"], nu_plain=pl["nu"],
+                   speedup_vs_plain=pl["wall_s"] / (warm["wall_s"] + t_inf),
+                   nu_rel_diff_plain=np.abs(warm["nu"] - pl["nu"]) / np.abs(pl["nu"]))
+    return out
 
 
 def main(argv=None):
