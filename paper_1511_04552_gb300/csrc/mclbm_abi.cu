@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "mclbm_internal.h"
+#include "nvtx_range.h"
 
 using namespace mcl;
 
@@ -304,6 +305,7 @@ int mclbm_init(mclbm_t* h, int mode, const float* warm_dev) {
 }
 
 int mclbm_step(mclbm_t* h, int64_t n) {
+  mcl::NvtxRange range("mclbm_step");
   int rc = ready(h, true);
   if (rc) return rc;
   if (n < 0) return fail(h, MCLBM_EINVAL, "negative step count");
@@ -797,6 +799,7 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
 }
 
 int mclbm_batch_step(mclbm_batch_t* b, int64_t n) {
+  mcl::NvtxRange range("mclbm_batch_step");
   if (!b) return MCLBM_EINVAL;
   if (n < 0 || (n & 1)) return bfail(b, MCLBM_EINVAL, "batch step counts must be even");
   BCK(b, cudaSetDevice(b->device));

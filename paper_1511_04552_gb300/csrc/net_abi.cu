@@ -14,6 +14,7 @@
 #include "../../include/mclbm.h"
 #include "../../include/mclbm_net.h"
 #include "net_internal.h"
+#include "nvtx_range.h"
 
 using namespace mcl::net;
 
@@ -599,6 +600,7 @@ int mclbm_net_field_stats(mclbm_net_t* n, int count, const float* cond, const fl
 }
 
 int mclbm_net_forward(mclbm_net_t* n, int batch, const float* cond, float* fields) {
+  mcl::NvtxRange range("mclbm_net_forward");
   int rc = check_call(n, batch);
   if (rc != MCLBM_OK) return rc;
   if (!cond || !fields) return fail(n, MCLBM_EINVAL, "null pointer");
@@ -611,6 +613,7 @@ int mclbm_net_forward(mclbm_net_t* n, int batch, const float* cond, float* field
 
 int mclbm_net_loss_grad(mclbm_net_t* n, int batch, const float* cond, const float* target,
                         float* grad, double* loss) {
+  mcl::NvtxRange range("mclbm_net_loss_grad");
   int rc = check_call(n, batch);
   if (rc != MCLBM_OK) return rc;
   if (!cond || !target || !grad || !loss) return fail(n, MCLBM_EINVAL, "null pointer");
@@ -625,6 +628,7 @@ int mclbm_net_loss_grad(mclbm_net_t* n, int batch, const float* cond, const floa
 
 int mclbm_net_train_step(mclbm_net_t* n, int batch, const float* cond, const float* target,
                          float lr, double* loss) {
+  mcl::NvtxRange range("mclbm_net_train_step");
   int rc = check_call(n, batch);
   if (rc != MCLBM_OK) return rc;
   if (!cond || !target || !(lr > 0.f)) return fail(n, MCLBM_EINVAL, "bad argument");
