@@ -261,6 +261,13 @@ int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);
 int mclbm_save(mclbm_t *h, const char *path);
 int mclbm_load(mclbm_t *h, const char *path);
 
+/* Self-test of failure detection, no handle needed: launches one kernel that waits with the
+ * step kernels' bounded mbarrier wait on a barrier nothing arrives on; the wait gives up after
+ * about 2 s and the kernel returns normally. Returns MCLBM_ETIMEOUT when that happened as
+ * designed (the code every stuck step reports), MCLBM_ECUDA otherwise; *seconds (may be NULL)
+ * receives the host-measured duration. Syncs the given stream (NULL: legacy default stream). */
+int mclbm_selftest_wait_timeout(void *cuda_stream, double *seconds);
+
 /* Time steps done since the last mclbm_init or mclbm_state_set (-1 for a NULL handle). */
 int64_t mclbm_steps_done(const mclbm_t *h);
 

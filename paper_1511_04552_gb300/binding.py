@@ -27,6 +27,7 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
            "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
            "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc", "mclbm_save", "mclbm_load",
+           "mclbm_selftest_wait_timeout",
            "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
            "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
            "mclbm_batch_last_error", "mclbm_batch_destroy",
@@ -105,6 +106,8 @@ def lib():
         L.mclbm_state_set.argtypes = [vp, vp]
         L.mclbm_run_host.argtypes = [vp, fp, C.c_int64, C.c_uint32, fp, dp, dp]
         L.mclbm_get_consts.argtypes = [vp, C.POINTER(Consts)]
+        L.mclbm_selftest_wait_timeout.argtypes = [vp, dp]
+        L.mclbm_selftest_wait_timeout.restype = C.c_int
         L.mclbm_save.argtypes = [vp, C.c_char_p]
         L.mclbm_load.argtypes = [vp, C.c_char_p]
         L.mclbm_save.restype = C.c_int

@@ -282,3 +282,20 @@ def test_checkpoint_resume_is_bitwise(storage, tmp_path):
     with pytest.raises(m.MclbmError) as e:
         d.load(path)
     assert e.value.code == m.binding.EINVAL
+
+
+def test_bounded_wait_gives_up_and_reports():
+    """Failure detection without a fault: the step kernels' bounded mbarrier wait, on a barrier
+    that nothing arrives on, gives up after about 2 s and reports MCLBM_ETIMEOUT; the context
+    stays usable (a cavity steps afterwards)."""
+    import ctypes as C
+    import torch
+    import paper_1511_04552_gb300 as m
+    secs = C.c_double()
+    st = torch.cuda.current_stream()
+    rc = m.lib().mclbm_selftest_wait_timeout(C.c_void_p(st.cuda_stream), C.byref(secs))
+    assert rc == m.binding.ETIMEOUT
+    assert 0.1 < secs.value < 10.0, secs.value
+    cav = m.Cavity(32, 32, 1e3, 6.2, 0.01, 20e-9).init()
+    cav.step(10)
+    assert np.isfinite(cav.nusselt()[0])
