@@ -358,10 +358,26 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--bench-train", type=int, default=0,
                     help="only time this many training steps on synthetic targets and exit")
+    ap.add_argument("--evaluate", default=None,
+                    help="only evaluate these weights on --held-out points (seed --seed + 1)")
+    ap.add_argument("--plain", action="store_true",
+                    help="with --evaluate: also solve every point cold on its own")
     a = ap.parse_args(argv)
     log = lambda s: print(s, flush=True)  # noqa: E731
     if a.bench_train:
         log(json.dumps(bench_train(a.bench_train, ny=a.size, nx=a.size)))
+        return
+    if a.evaluate:
+        net = WarmNet.load(a.evaluate)
+        held = sample_conditions(a.held_out, a.seed + 1)
+        ev = evaluate(net, held, group=a.group, tol=a.tol, ny=net.ny, nx=net.nx, plain=a.plain)
+        summary = {k: (v.tolist() if isinstance(v, np.ndarray) else v) for k, v in ev.items()}
+        log(json.dumps({k: summary[k] for k in ("n", "cold_wall_s", "warm_wall_s", "speedup_wall",
+                                                "speedup_steps", "plain_wall_s",
+                                                "speedup_vs_plain") if k in summary}))
+        if a.report:
+            with open(a.report, "w") as f:
+                json.dump(summary, f)
         return
     conds = sample_conditions(a.train, a.seed)
     t0 = time.perf_counter()
