@@ -171,3 +171,21 @@ def test_predicted_masses_are_the_cold_starts():
     for ch in (3, 4):
         d = f[:, ch] - raw[:, ch]
         assert np.ptp(d[0]) < 1e-14 and np.ptp(d[1]) < 1e-14
+
+
+def test_conv_flop_count_matches_the_network_definition():
+    """warmstart.conv_flops (the training benchmark's FLOP count) against a count taken from
+    the oracle's layer list: 2 multiply-adds per weight per output pixel."""
+    from paper_1511_04552_gb300.warmstart import conv_flops, sample_conditions
+    c0, ny, nx, batch = 16, 256, 256, 3
+    grid = {"e0": 1, "e1": 2, "e2": 4, "e3": 8, "e4": 16, "d3": 8, "d2": 4, "d1": 2, "d0": 1,
+            "out": 1}
+    ref = 0.0
+    for name, cu, cs, co, _, _, _ in WN.layers(c0):
+        s = grid[name]
+        ref += 2.0 * batch * (ny // s) * (nx // s) * co * 9 * (cu + cs)
+    assert conv_flops(ny, nx, c0, batch) == ref
+    c = sample_conditions(500, 4)
+    assert np.all((c[:, 0] >= 1e3) & (c[:, 0] <= 1e6))
+    assert np.all((c[:, 1] >= 0.0) & (c[:, 1] <= 0.05))
+    assert np.all((c[:, 2] >= 10e-9) & (c[:, 2] <= 100e-9))
