@@ -67,3 +67,13 @@ def test_slow_mode_behind_a_fast_one():
     seq = 3.0 + 0.5 * np.exp(-t / 3.0) + 2e-3 * np.exp(-t / 300.0)
     n = _first_stop(seq)
     assert n is not None and abs(seq[n - 1] - 3.0) <= 1e-4 * 3.0
+
+
+def test_ablation_cases_keep_drag_and_buoyancy():
+    from paper_1511_04552_gb300 import binding as B
+    from paper_1511_04552_gb300.studies import ABLATION
+    masks = [m for _, m in ABLATION]
+    assert len(set(masks)) == len(masks) and masks[0] == B.F_ALL
+    for m in masks:
+        assert m & B.F_DRAG and m & B.F_BUOYANCY and 0 < m <= B.F_ALL
+    assert sorted(bin(B.F_ALL ^ m).count("1") for m in masks) == [0, 1, 1, 1, 1, 1]
