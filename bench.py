@@ -381,7 +381,7 @@ def main():
     e2e_value = whole_job_rate(nx * ny * CH * args.steps, ws, e2e_time)
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and ws == 1:  # the scaling runs report the main line
         # HBM case: 1024^2, state larger than L2
         w4 = workloads.CAVITY_1024
         big = m.Cavity(w4["nx"], w4["ny"], w4["Ra"], w4["Pr"], w4["phi"], w4["d_p"])
