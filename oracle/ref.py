@@ -4,7 +4,6 @@ TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU-bas
 it. It shares no code with the CUDA library and never imports it.
 """
 import ctypes as C
-import os
 
 import numpy as np
 

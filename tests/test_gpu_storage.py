@@ -1,7 +1,6 @@
 """16-bit population storage (FP16 / BF16 holding 2^12 x the deviations, FP32 arithmetic):
 exact round trips, identical results from both step kernels, and accuracy against the FP64
 oracle within the reduced-storage target (mean Nusselt number within 0.5 %)."""
-import numpy as np
 import pytest
 
 import workloads
