@@ -188,11 +188,10 @@ int mclbm_state_set(mclbm_t *h, const float *dev_in);
 int mclbm_run_host(mclbm_t *h, const float *warm_host, int64_t n, uint32_t which,
                    float *fields_host, double *nu_hot, double *nu_cold);
 
-/* Component masses for callers that cannot allocate device memory: code that runs where
- * cudaMalloc is not allowed or not wanted, such as inside a stream capture, in a host
- * application that hands out all device memory from its own fixed pool, or in a loop that
- * must not pay for, or synchronise on, an allocation. Not a method of the paper (it has no
- * counterpart there): the same FP64 sums as mclbm_mass, needing no handle and no buffer.
+/* Component masses for callers that cannot allocate device memory: a host application that
+ * hands out all device memory from its own fixed pool and forbids other allocations, or a
+ * loop that must not pay for an allocation on every call. Not a method of the paper (it has
+ * no counterpart there): the same FP64 sums as mclbm_mass, needing no handle and no buffer.
  *   state_dev: caller-owned device array [27][ny][nx] FP32 in the layout of mclbm_state_get
  *              (deviations from the rest state; only the 18 f planes are read).
  *   rho_w0, rho_p0: the rest-state partial densities (mclbm_consts) added back per node.
@@ -203,7 +202,11 @@ int mclbm_run_host(mclbm_t *h, const float *warm_host, int64_t n, uint32_t which
  * device current), so make that first call before any stream capture. Calls that overlap on
  * the GPU share the array and race: serialise them (one stream, or wait in between). Every
  * scratch element a call reads is written earlier by the same call, so a previous call's
- * contents never leak into a result. Calls no cudaMalloc or cudaFree. Syncs the stream.
+ * contents never leak into a result. Calls no cudaMalloc or cudaFree. Host-synchronous: it
+ * copies the two totals to host memory and waits for the stream before it returns.
+ * It reads a raw state and never sees a handle's error word: after a step kernel gave up a
+ * bounded wait (MCLBM_ETIMEOUT from mclbm_mass, mclbm_nusselt or mclbm_residual) the state is
+ * partly written, so check the handle's status with one of those before trusting this result.
  * Returns MCLBM_OK, MCLBM_EINVAL, MCLBM_ETOOLARGE, MCLBM_ECUDA or MCLBM_EDIVERGED. */
 int mclbm_mass_noalloc(const float *state_dev, int nx, int ny, double rho_w0, double rho_p0,
                        double *mass_w, double *mass_p, void *cuda_stream);

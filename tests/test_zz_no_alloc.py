@@ -1,8 +1,8 @@
 """mclbm_mass_noalloc against mclbm_mass, through the C ABI.
 
-mclbm_mass_noalloc serves callers that cannot allocate device memory (inside a stream
-capture, under a host framework that owns all device memory, or in a loop that must not pay
-for an allocation): it keeps its partial sums in a static device array instead of a bound
+mclbm_mass_noalloc serves callers that cannot allocate device memory (a host application
+that owns all device memory in its own fixed pool, or a loop that must not pay for an
+allocation per call): it keeps its partial sums in a static device array instead of a bound
 buffer. This file is named to be collected last, so that a run which stops at the first
 failure has already run every other test.
 """
@@ -26,9 +26,10 @@ def test_mass_noalloc_matches_mclbm_mass_twice():
     P.ensure_built()
     import paper_1511_04552_gb300 as m
     L = m.lib()
-    # two calls in a row: a taller lattice first, then a shorter one, so rows left in the
-    # shared scratch by the first call would show up in the second if they leaked
-    for nx, ny, steps in [(96, 70, 333), (40, 23, 57)]:
+    # calls in a row: a taller lattice first, then shorter ones, so rows left in the shared
+    # scratch by an earlier call would show up in a later one if they leaked; the first has
+    # more rows than the row kernel has CTAs (1024), so its grid-stride loop runs
+    for nx, ny, steps in [(16, 2100, 40), (96, 70, 333), (40, 23, 57)]:
         cav = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9).init()
         cav.step(steps)
         ref_w, ref_p = cav.mass()
