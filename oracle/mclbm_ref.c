@@ -50,8 +50,11 @@
  * thermal LBM and against the de Vahl Davis cavity benchmark, the conduction limit, the drag
  * impulse against the two-body ODE, the interaction-force balance, centro-symmetry, the
  * SI-to-lattice constants against an independent derivation, Poiseuille curvature, the
- * thermophoretic terminal drift and the Brownian drift flux. The Saffman and Magnus forces are
- * pinned only by invariants (direction, zeros, linearity); beyond that their parity is unpinned.
+ * thermophoretic terminal drift, the Brownian drift flux, the Saffman lift against Saffman's
+ * sphere lift per radius and its scaling exponents, the Magnus migration in SI and its
+ * exponents, the gravity (weight less buoyancy) and Boussinesq (Eq 9) force densities in SI
+ * through one step's momentum change, the local thermal relaxation time (Eq 24) and the
+ * residual recomputed from field snapshots.
  */
 #include "mclbm_ref.h"
 

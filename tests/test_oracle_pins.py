@@ -451,3 +451,233 @@ def test_warm_init_with_density(oracle_mod):
     w[4] = 1.0 - w[3]
     r = oracle_mod.RefSolver(nx, ny, 1e4, 6.2, 0.02, 30e-9).init(warm=w)
     np.testing.assert_array_equal(r.get_state(), s4)
+
+
+# ---------------------------------------------------------------- Table 1 magnitudes
+# A uniform state: every node holds the same equilibrium populations, so the nodes that touch
+# no wall see exactly these populations after streaming and every gradient there is zero.
+def _uniform_state(nx, ny, rho_w, uw, rho_p, up, theta, u_g=(0.0, 0.0), g_extra=None):
+    def feq(rho, u):
+        eu = E[:, 0] * u[0] + E[:, 1] * u[1]
+        return W * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u[0] ** 2 + u[1] ** 2))
+    node = np.concatenate([feq(rho_w, uw), feq(rho_p, up), feq(theta, u_g)])
+    if g_extra is not None:
+        node[18:] += g_extra
+    return np.broadcast_to(node[:, None, None], (27, ny, nx)).copy()
+
+
+def _set_uniform(s, nx, ny, **kw):
+    s.init()
+    s.set_state(_uniform_state(nx, ny, **kw))
+    return s
+
+
+def _si_scales(nx, ny, Ra, Pr, phi, d):
+    ind = _independent_constants(nx, ny, Ra, Pr, phi, d)
+    ind["vel"] = ind["dx"] / ind["dt"]
+    return ind
+
+
+def test_saffman_lift_is_saffmans_sphere_lift(oracle_mod):
+    """Table 1 Saffman lift (K_S/4) mu |w| d_p^2 sqrt(rho gamma/mu) with K_S = 81.2 is Saffman's
+    lift on a sphere of radius a = d_p/2 in his original form, 81.2 mu a^2 |w| sqrt(gamma/nu):
+    the same magnitude written per radius. Per volume it is n_p = phi/V_p times that, with the
+    shear rate gamma = 8 |u^p|/H; it points along the slip turned by +90 degrees."""
+    nx = ny = 12
+    Ra, Pr, phi, d = 1e5, 6.2, 0.03, 30e-9
+    s = ref_solver(oracle_mod, nx, ny, Ra=Ra, Pr=Pr, phi=phi, d_p=d,
+                   force_mask=oracle_mod.F_SAFFMAN)
+    c = s.consts()
+    si = _si_scales(nx, ny, Ra, Pr, phi, d)
+    rho_w, rho_p = 0.95 * c["rho_w0"], 1.2 * c["rho_p0"]
+    uw, up = np.array([2e-3, -1e-3]), np.array([5e-4, 1.5e-3])
+    _set_uniform(s, nx, ny, rho_w=rho_w, uw=uw, rho_p=rho_p, up=up, theta=0.1)
+    t = s.node_terms(6, 5)
+    np.testing.assert_allclose(t["uw"], uw, rtol=1e-12)
+    np.testing.assert_allclose(t["up"], up, rtol=1e-12)
+    w = (uw - up) * si["vel"]                               # slip, m/s
+    gamma = 8 * np.linalg.norm(up) * si["vel"] / si["H_phys"]
+    nu_ns = si["mu_ns"] / si["rho_ns"]
+    a = d / 2
+    lift = 81.2 * si["mu_ns"] * a * a * np.linalg.norm(w) * math.sqrt(gamma / nu_ns)  # N
+    n_p = (rho_p * 997.1 / 3970.0) / (math.pi * d ** 3 / 6)
+    direction = np.array([-w[1], w[0]]) / np.linalg.norm(w)
+    expect = n_p * lift * si["C_F"] * direction
+    np.testing.assert_allclose(t["F_S"], expect, rtol=1e-12)
+
+
+def _saffman_at(oracle_mod, uw, up, d, nx=12, ny=12):
+    s = ref_solver(oracle_mod, nx, ny, Ra=1e5, Pr=6.2, phi=0.03, d_p=d,
+                   force_mask=oracle_mod.F_SAFFMAN)
+    c = s.consts()
+    _set_uniform(s, nx, ny, rho_w=c["rho_w0"], uw=np.asarray(uw), rho_p=c["rho_p0"],
+                 up=np.asarray(up), theta=0.0)
+    return s.node_terms(6, 6)["F_S"]
+
+
+def test_saffman_scaling_exponents(oracle_mod):
+    """The lift is linear in the slip, goes as the square root of the particle speed (through
+    the shear rate 8 |u^p|/H), and per unit volume as 1/d_p (n_p d_p^2 ~ d_p^-1)."""
+    uw, up, d = np.array([1e-3, 2e-3]), np.array([-4e-4, 7e-4]), 30e-9
+    F = _saffman_at(oracle_mod, uw, up, d)
+    # slip x 3 at the same particle velocity
+    F3 = _saffman_at(oracle_mod, up + 3 * (uw - up), up, d)
+    np.testing.assert_allclose(F3, 3 * F, rtol=1e-12)
+    # particle velocity x 4 at the same slip: sqrt(4) = 2
+    F4 = _saffman_at(oracle_mod, uw + 3 * up, 4 * up, d)
+    np.testing.assert_allclose(F4, 2 * F, rtol=1e-12)
+    # particle diameter x 2
+    F2 = _saffman_at(oracle_mod, uw, up, 2 * d)
+    np.testing.assert_allclose(F2, 0.5 * F, rtol=1e-12)
+
+
+def _magnus_row(oracle_mod, uw, up, d, nx=40, ny=40, j=20, cols=range(1, 15)):
+    s = ref_solver(oracle_mod, nx, ny, Ra=1e5, Pr=6.2, phi=0.03, d_p=d,
+                   force_mask=oracle_mod.F_MAGNUS)
+    c = s.consts()
+    _set_uniform(s, nx, ny, rho_w=c["rho_w0"], uw=np.asarray(uw), rho_p=c["rho_p0"],
+                 up=np.asarray(up), theta=0.0)
+    return np.array([s.node_terms(i, j)["F_M"] for i in cols])
+
+
+def test_magnus_migration_magnitude(oracle_mod):
+    """Table 1 Magnus migration v_M = 0.34 (vbar^2 H/nu)(d_p/H)^2.84 (2z/H)(0.63 - 2z/H) along the
+    inward normal of the nearest wall, with vbar = |u^w + u^p|/2 and z the distance to that wall,
+    acting through m_dot_p = m_p beta_St: per unit volume phi rho_p beta_St v_M. Evaluated in SI
+    with independently derived scales, along a row whose nearest wall is the hot wall."""
+    nx = ny = 40
+    Ra, Pr, phi, d = 1e5, 6.2, 0.03, 30e-9
+    uw, up = np.array([3e-3, -2e-3]), np.array([2.5e-3, -1e-3])
+    cols = list(range(1, 15))
+    FM = _magnus_row(oracle_mod, uw, up, d, cols=cols)
+    si = _si_scales(nx, ny, Ra, Pr, phi, d)
+    H = si["H_phys"]
+    nu_ns = si["mu_ns"] / si["rho_ns"]
+    vbar = 0.5 * np.linalg.norm(uw + up) * si["vel"]
+    beta_st = 18 * si["mu_ns"] / (3970.0 * d * d)
+    phi_loc = phi  # the node holds the initial partial density
+    for k, i in enumerate(cols):
+        z = (i + 0.5) * si["dx"]
+        zh = 2 * z / H
+        v_M = 0.34 * (vbar ** 2 * H / nu_ns) * (d / H) ** 2.84 * zh * (0.63 - zh)
+        expect = phi_loc * 3970.0 * beta_st * v_M * si["C_F"]
+        assert abs(FM[k][0] - expect) <= 1e-12 * abs(expect) + 1e-30
+        assert FM[k][1] == 0.0
+
+
+def test_magnus_scaling_exponents(oracle_mod):
+    """Per unit volume the Magnus force goes as d_p^0.84 (beta_St ~ d_p^-2 times (d_p/H)^2.84),
+    as vbar^2, and along the wall normal as the profile (2z/H)(0.63 - 2z/H)."""
+    uw, up, d = np.array([3e-3, -2e-3]), np.array([2.5e-3, -1e-3]), 30e-9
+    cols = list(range(1, 15))
+    F = _magnus_row(oracle_mod, uw, up, d, cols=cols)[:, 0]
+    F2 = _magnus_row(oracle_mod, uw, up, 2 * d, cols=cols)[:, 0]
+    np.testing.assert_allclose(F2, 2 ** 0.84 * F, rtol=1e-12)
+    Fv = _magnus_row(oracle_mod, 2 * uw, 2 * up, d, cols=cols)[:, 0]
+    np.testing.assert_allclose(Fv, 4 * F, rtol=1e-12)
+    zh = 2 * (np.array(cols) + 0.5) / 40
+    prof = zh * (0.63 - zh)
+    ratio = F / prof
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-12)
+    assert np.all(np.sign(F) == np.sign(prof))
+
+
+def test_gravity_is_table1_weight_less_buoyancy(oracle_mod):
+    """Table 1 gravity -V_p (rho_p - rho_f) g per particle, n_p = phi/V_p per volume: with only
+    gravity on, one step changes the particle momentum at a node by exactly that force density
+    (converted with an independently derived force scale), downward, and the fluid's by the
+    uniform part phi_0 (rho_p - rho_f) g upward (the Boussinesq reference), so a node's total is
+    the weight of its particle excess only."""
+    nx = ny = 10
+    Ra, Pr, phi, d = 1e4, 6.2, 0.02, 40e-9
+    s = ref_solver(oracle_mod, nx, ny, Ra=Ra, Pr=Pr, phi=phi, d_p=d,
+                   force_mask=oracle_mod.F_GRAVITY)
+    c = s.consts()
+    si = _si_scales(nx, ny, Ra, Pr, phi, d)
+    rho_p = 1.25 * c["rho_p0"]
+    z2 = np.zeros(2)
+    _set_uniform(s, nx, ny, rho_w=c["rho_w0"], uw=z2, rho_p=rho_p, up=z2, theta=0.0)
+    s.step(1)
+    st = s.get_state()
+    i, j = 4, 5
+    dmp = (st[9:18, j, i][:, None] * E).sum(0)   # particle momentum after one step (it was 0)
+    dmw = (st[0:9, j, i][:, None] * E).sum(0)
+    phi_loc = rho_p * 997.1 / 3970.0
+    g = 9.81
+    Fp = -phi_loc * (3970.0 - 997.1) * g * si["C_F"]
+    Fw = phi * (3970.0 - 997.1) * g * si["C_F"]
+    assert Fp < 0 < Fw
+    assert abs(dmp[1] - Fp) <= 1e-12 * abs(Fp) and abs(dmp[0]) < 1e-16
+    assert abs(dmw[1] - Fw) <= 1e-12 * abs(Fw) and abs(dmw[0]) < 1e-16
+    assert abs((dmp + dmw)[1] + 0.25 * Fw) <= 1e-11 * abs(Fw)
+
+
+def test_buoyancy_uses_eq9_expansion(oracle_mod):
+    """Eq 2's Boussinesq force rho_ns beta_ns g (T - T_ref) with the volume-weighted expansion
+    coefficient of Eq 9, evaluated in SI (T - T_ref = theta dT) and converted with an
+    independently derived force scale."""
+    nx = ny = 10
+    Ra, Pr, phi, d = 1e4, 6.2, 0.04, 40e-9
+    s = ref_solver(oracle_mod, nx, ny, Ra=Ra, Pr=Pr, phi=phi, d_p=d,
+                   force_mask=oracle_mod.F_BUOYANCY)
+    c = s.consts()
+    si = _si_scales(nx, ny, Ra, Pr, phi, d)
+    beta_ns = phi * 0.85e-5 + (1 - phi) * 2.1e-4       # Eq 9 as printed
+    assert abs(c["beta_ratio"] - beta_ns / 2.1e-4) <= 1e-14
+    rho_w, rho_p, theta = 0.97 * c["rho_w0"], 1.1 * c["rho_p0"], 0.3
+    z2 = np.zeros(2)
+    _set_uniform(s, nx, ny, rho_w=rho_w, uw=z2, rho_p=rho_p, up=z2, theta=theta)
+    t = s.node_terms(5, 4)
+    assert abs(t["theta"] - theta) < 1e-15
+    rho_si = (rho_w + rho_p) * 997.1
+    expect = rho_si * beta_ns * 9.81 * theta * 10.0 * si["C_F"]
+    assert abs(t["F_buoy"][1] - expect) <= 1e-12 * expect and t["F_buoy"][0] == 0.0
+
+
+@pytest.mark.parametrize("scale_p", [0.5, 2.0])
+def test_thermal_relaxation_uses_local_mass_fractions(oracle_mod, scale_p):
+    """Eq 24 with the local mass fractions of Eq 25: a node whose particle partial density differs
+    from the initial one relaxes g towards its equilibrium at tau_theta = Y_w tau_theta^w +
+    Y_p tau_theta^p of its own fractions (not of the initial ones)."""
+    nx = ny = 8
+    Ra, Pr, phi, d = 1e4, 6.2, 0.04, 30e-9
+    s = ref_solver(oracle_mod, nx, ny, Ra=Ra, Pr=Pr, phi=phi, d_p=d, force_mask=0)
+    c = s.consts()
+    ind = _independent_constants(nx, ny, Ra, Pr, phi, d)
+    rho_w, rho_p, theta = c["rho_w0"], scale_p * c["rho_p0"], 0.2
+    # a non-equilibrium part with zero sum (theta unchanged) and a heat flux
+    delta = np.array([0.0, 1.0, -0.5, -1.0, 0.5, 0.25, -0.25, -0.25, 0.25]) * 1e-3
+    delta[0] = -delta[1:].sum()
+    z2 = np.zeros(2)
+    _set_uniform(s, nx, ny, rho_w=rho_w, uw=z2, rho_p=rho_p, up=z2, theta=theta,
+                 g_extra=delta)
+    s.step(1)
+    g_after = s.get_state()[18:, 4, 3]
+    d_after = g_after - W * theta
+    tau = delta[1:] / (delta[1:] - d_after[1:])
+    Yw, Yp = rho_w / (rho_w + rho_p), rho_p / (rho_w + rho_p)
+    expect = Yw * ind["tau_tw"] + Yp * ind["tau_tp"]
+    np.testing.assert_allclose(tau, expect, rtol=1e-10)
+    # the initial fractions' tau differs by far more than the 1e-10 this test resolves
+    at_initial = ind["tau_tw"] * c["Y_w0"] + ind["tau_tp"] * c["Y_p0"]
+    assert abs(expect - at_initial) > 1e-5 * at_initial
+
+
+def test_residual_from_field_snapshots(oracle_mod):
+    """The steady-state residual: max over u, theta and phi of ||q_now - q_then||_2 /
+    (K ||q_now||_2), K the steps between the two snapshots, recomputed from the fields."""
+    s = ref_solver(oracle_mod, 20, 16, Ra=1e4, phi=0.02, d_p=30e-9).init()
+    s.step(150)
+    s.residual()  # snapshot at step 150
+    which = oracle_mod.UX | oracle_mod.UY | oracle_mod.THETA | oracle_mod.PHI
+    then = s.fields(which)
+    s.step(70)
+    now = s.fields(which)
+    r = s.residual()
+    K = 70
+    terms = []
+    for sel in ([0, 1], [2], [3]):
+        num = np.sqrt(((now[sel] - then[sel]) ** 2).sum())
+        den = np.sqrt((now[sel] ** 2).sum())
+        terms.append(num / (K * den))
+    assert r > 0 and abs(r - max(terms)) <= 1e-12 * r
