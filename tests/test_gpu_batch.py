@@ -90,3 +90,49 @@ def test_sweep_to_steady_small():
         alone = m.Cavity(nx, nx, Ra, 6.2, phi, d).init()
         r = m.run_to_steady(alone, tol=1e-4, check_every=1000)
         assert abs(r["nu_hot"] - res["nu_hot"][k]) <= 1e-3 * r["nu_hot"]
+
+
+ORACLE_CASES = [dict(nx=64, ny=64, Ra=1e5, phi=0.03, d_p=30e-9),
+                dict(nx=96, ny=40, Ra=1e4, phi=0.01, d_p=10e-9),
+                dict(nx=130, ny=67, Ra=1e3, phi=0.04, d_p=100e-9),
+                dict(nx=70, ny=33, Ra=3e5, phi=0.02, d_p=50e-9)]
+ORACLE_STEPS = 2000
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """Each case of the batch solved alone by the FP64 oracle from the same seeded state."""
+    import oracle
+    import workloads
+    out = []
+    for k, c in enumerate(ORACLE_CASES):
+        warm = workloads.perturbed_rest_fields(c["nx"], c["ny"], c["phi"], seed=10 + k)
+        ref = oracle.RefSolver(c["nx"], c["ny"], c["Ra"], 6.2, c["phi"], c["d_p"])
+        ref.init(warm=warm.astype(np.float64)).step(ORACLE_STEPS)
+        out.append((warm, ref.fields(P.ALL_FIELDS), ref.nusselt()))
+    return out
+
+
+# FP32 storage: the batch kernel is held to the single-cavity parity bar (1e-5 per field and
+# per Nusselt number); FP16 storage with stochastic rounding to the bounds of the storage tests.
+@pytest.mark.parametrize("storage,field_tol,nu_tol", [(0, P.FIELD_RTOL, P.NU_RTOL),
+                                                      (1, 5e-3, 5e-3)])
+def test_batch_matches_fp64_oracle(storage, field_tol, nu_tol, oracle_runs):
+    """Four cavities of different sizes, Ra, phi and d_p (the paper's parametric sweeps) in one
+    batch, 2000 steps from seeded states, each against its own FP64 oracle run."""
+    import torch
+    import paper_1511_04552_gb300 as m
+    cavs = []
+    for c, (warm, _, _) in zip(ORACLE_CASES, oracle_runs):
+        cav = m.Cavity(c["nx"], c["ny"], c["Ra"], 6.2, c["phi"], c["d_p"], storage=storage)
+        cavs.append(cav.init(warm=torch.from_numpy(warm).cuda()))
+    b = m.Batch(cavs)
+    b.step(ORACLE_STEPS)
+    hot, cold = b.nusselt()
+    for k, (cav, (_, r, (rh, rc))) in enumerate(zip(cavs, oracle_runs)):
+        g = cav.fields(P.ALL_FIELDS).cpu().numpy()
+        errs = {name: P.rel_l2(g[i], r[i]) for i, name in enumerate(P.FIELD_NAMES)}
+        print("case", k, "storage", storage, "Nu %.2e" % (abs(hot[k] - rh) / rh), errs)
+        bad = {n: e for n, e in errs.items() if not e <= field_tol}
+        assert not bad, (k, bad)
+        assert abs(hot[k] - rh) <= nu_tol * abs(rh) and abs(cold[k] - rc) <= nu_tol * abs(rc)
