@@ -34,6 +34,14 @@ STORAGE = {"f32": (0, 216), "f16": (1, 108), "bf16": (2, 108)}  # (code, bytes p
 CHUNK = 1000        # time steps per benchmark step (one residual / Nusselt check interval)
 OUR_KERNELS_PER_REDUCTION = 5  # nusselt, residual + final, mass + final
 WORKLOADS = {"cavity256": workloads.CAVITY_256, "cavity1024": workloads.CAVITY_1024}
+STEP_SOURCES = ("mclbm_device.cuh", "mclbm_pair.cuh")  # the step kernels' source
+
+
+def nodes_per_thread(nx, ny, sms):
+    """The step kernel's nodes per thread (the library's rule): one while the lattice gives
+    every SM at most two 32 x 8 tiles, two beyond."""
+    tiles = ((nx + 31) // 32) * ((ny + 7) // 8)
+    return 1 if tiles <= 2 * sms else 2
 
 
 def parse():
@@ -211,10 +219,13 @@ def ncu_traffic(workload_name):
     """DRAM bytes per step launch (FP32 storage) from the committed ncu summary, if it was
     taken on the current step-kernel source (else None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1511_04552_gb300", "csrc", "mclbm_device.cuh")
+    csrc = os.path.join(ROOT, "paper_1511_04552_gb300", "csrc")
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in STEP_SOURCES:
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        sha = h.hexdigest()[:16]
         vals = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
@@ -364,6 +375,7 @@ def main():
     lu = nx * ny * CH * args.steps
     value = whole_job_rate(lu, ws, elapsed)
     hbm_peak, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     achieved = bytes_lu * nx * ny / step_time / 1e9
 
     # end to end through the C ABI with host buffers: H2D warm fields, init, 1000 steps,
@@ -392,7 +404,9 @@ def main():
             "workload": w4["name"], "mlups": w4["nx"] * w4["ny"] / t_big / 1e6,
             "roofline": {"bound": "hbm", "achieved": ach_big, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach_big / hbm_peak, "traffic": ncu_traffic(w4["name"]),
-                         "peak_kind": peak_kind, "bytes_per_launch": BYTES_PER_LU * w4["nx"] * w4["ny"],
+                         "peak_kind": peak_kind, "kernel": "step_pair_tma_kernel",
+                         "nodes_per_thread": nodes_per_thread(w4["nx"], w4["ny"], sms),
+                         "bytes_per_launch": BYTES_PER_LU * w4["nx"] * w4["ny"],
                          "launch_us": t_big * 1e6}}
         del big
         torch.cuda.empty_cache()
@@ -429,7 +443,9 @@ def main():
                          "frac": achieved / hbm_peak,
                          "traffic": ncu_traffic(w["name"]) if args.storage == "f32" else None,
                          "peak_kind": peak_kind,
-                         "kernel": "step_tma_kernel", "bytes_per_launch": bytes_lu * nx * ny,
+                         "kernel": "step_pair_tma_kernel",
+                         "nodes_per_thread": nodes_per_thread(nx, ny, sms),
+                         "bytes_per_launch": bytes_lu * nx * ny,
                          "launch_us": step_time * 1e6},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * nx * ny * 4,

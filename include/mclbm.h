@@ -242,8 +242,9 @@ int mclbm_batch_nusselt(mclbm_batch_t *b, double *nu_hot, double *nu_cold);
 int mclbm_batch_set_active(mclbm_batch_t *b, const int *active);
 
 /* Autotuner: times steps_per_trial (even) steps for each tile order (0: cavity by cavity,
- * 1: largest first, 2: interleaved) and 1 or 2 CTAs per SM, keeps the fastest and reports it.
- * The trial steps are real steps: every active cavity advances 2 x 6 x steps_per_trial. */
+ * 1: largest first, 2: interleaved) and each CTA count per SM from 1 to the most that fit (at
+ * most 4), keeps the fastest and reports it. The trial steps are real steps: every active
+ * cavity advances 2 x 3 x (CTA counts tried) x steps_per_trial. */
 int mclbm_batch_tune(mclbm_batch_t *b, int64_t steps_per_trial, int *order, int *ctas_per_sm);
 
 /* Text of the batch's latest error. */

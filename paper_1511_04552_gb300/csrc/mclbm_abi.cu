@@ -271,11 +271,11 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   // kernel if the device cannot run it
   h->cfg = choose_step_config(h->nx, h->ny);
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
-  if (h->cfg.variant == 2) {
+  if (h->cfg.variant % 10 == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
         make_state_tensor_map(h->tmap, h->state[0], h->L) != cudaSuccess) {
       cudaGetLastError();
-      h->cfg.variant = 0;
+      h->cfg.variant -= 2;
     }
   }
   CK(h, cudaMemsetAsync(h->err_dev, 0, 2 * sizeof(int), h->stream));
@@ -769,6 +769,7 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
     CUtensorMap maps[2];
     if (make_state_tensor_map(maps, h->state[0], h->L) != cudaSuccess) return bail(MCLBM_ECUDA);
     host[c].map = maps[0];
+    host[c].map_out = maps[1];
     host[c].level[0] = h->state[0];
     host[c].level[1] = h->state[1];
     host[c].L = h->L;
@@ -784,7 +785,7 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return bail(MCLBM_ECUDA);
   if (b->per_sm_max < 1) return bail(MCLBM_ECUDA);
-  b->per_sm = b->per_sm_max < 2 ? b->per_sm_max : 2;
+  b->per_sm = b->per_sm_max;
   b->bl.cavs = b->d_cavs;
   b->bl.tiles = b->d_tiles;
   b->bl.storage = cavities[0]->L.storage;
@@ -864,7 +865,7 @@ int mclbm_batch_tune(mclbm_batch_t* b, int64_t steps_per_trial, int* order_out,
   int best_order = b->order, best_per_sm = b->per_sm;
   int rc = MCLBM_OK;
   for (int order = 0; order < 3 && rc == MCLBM_OK; ++order)
-    for (int per_sm = 1; per_sm <= b->per_sm_max && per_sm <= 2 && rc == MCLBM_OK; ++per_sm) {
+    for (int per_sm = 1; per_sm <= b->per_sm_max && rc == MCLBM_OK; ++per_sm) {
       b->order = order;
       b->per_sm = per_sm;
       if ((rc = batch_retile(b))) break;

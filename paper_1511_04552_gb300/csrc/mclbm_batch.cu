@@ -1,8 +1,8 @@
 // Batched stepping of many cavities in one persistent launch per time step (the parametric
 // sweep: cavities of different sizes, Rayleigh numbers, volume fractions and particle sizes).
 // A tile table lists the 32 x 8 tiles of every active cavity; the persistent CTAs walk it
-// exactly like the single-cavity TMA kernel walks one cavity, reading each tile's cavity
-// arguments and tensor map from device memory. A batched reduction gives every cavity's
+// exactly like the single-cavity TMA kernel walks one cavity (the same tile loop), reading each
+// tile's cavity arguments and tensor maps from device memory. A batched reduction gives every cavity's
 // Nusselt numbers in one launch. The autotuner times a few tile orders and grid sizes.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -13,9 +13,10 @@
 #include <numeric>
 #include <vector>
 
-#include "mclbm_device.cuh"
+#include "mclbm_pair.cuh"
 
 namespace mcl {
+static_assert(pair::kTX == kTmaTX && pair::kTY == kTmaTY, "the tile table and the kernels share the tile shape");
 
 // Tile table entry: cavity (10 bits) | tile column (11 bits) | tile row (11 bits).
 __host__ __device__ constexpr uint32_t pack_tile(int c, int tx, int ty) {
@@ -25,30 +26,13 @@ __device__ __forceinline__ int tile_cav(uint32_t e) { return (int)(e >> 22); }
 __device__ __forceinline__ int tile_x(uint32_t e) { return (int)((e >> 11) & 2047u); }
 __device__ __forceinline__ int tile_y(uint32_t e) { return (int)(e & 2047u); }
 
+// One time step of every tile in the table: the single-cavity TMA tile loop (two nodes per
+// thread, one window per CTA reloaded as soon as the pulls have read it), with each tile's
+// tensor maps, layout, constants and destination level taken from its cavity's entry.
 template <class T, bool SR, bool ALLF>
-__global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
+__global__ void __launch_bounds__(pair::Threads<2>::value, pair::MinBlocks<2>::value)
     step_batch_kernel(const BatchCav* __restrict__ cavs, const uint32_t* __restrict__ tiles,
                       int n_tiles, int parity, uint32_t seed, const uint32_t* epoch, int* err) {
-  constexpr int TX = kTmaTX, TY = kTmaTY;
-  constexpr int NRING = 2 * TX + 2 * TY;
-  constexpr int XO = TmaTile<T>::XO;
-  constexpr uint32_t BYTES = TmaTile<T>::BYTES;
-  extern __shared__ __align__(128) unsigned char win_raw[];
-  __shared__ float s_th[TY + 2][TX + 2];
-  __shared__ float s_rp[TY + 2][TX + 2];
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ int s_abort;
-
-  const int t = threadIdx.x;
-  const int tx = t % TX, ty = t / TX;
-  const uint32_t bar0 = tma::smem_u32(&bars[0]);
-  const uint32_t win0 = tma::smem_u32(win_raw);
-  if (t == 0) {
-    tma::mbar_init(bar0, 1);
-    tma::mbar_init(bar0 + 8, 1);
-    tma::fence_barrier_init();
-    s_abort = 0;
-  }
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   uint32_t sh = 0u;
@@ -56,96 +40,18 @@ __global__ void __launch_bounds__(kTmaTX * kTmaTY, 2)
     const uint32_t ep = epoch ? *(volatile const uint32_t*)epoch : 0u;
     sh = mix32(seed ^ mix32(ep + 0x632BE5ABu));
   }
-  __syncthreads();
-
-  int hx = 0, hy = 0;
-  if (t < NRING) {
-    if (t < TX) {
-      hx = t;
-      hy = -1;
-    } else if (t < 2 * TX) {
-      hx = t - TX;
-      hy = TY;
-    } else if (t < 2 * TX + TY) {
-      hx = -1;
-      hy = t - 2 * TX;
-    } else {
-      hx = TX;
-      hy = t - 2 * TX - TY;
-    }
-  }
-
-  // the source level of cavity c this launch: its level at batch creation, flipped on odd launches
-  auto issue = [&](int tile, int stage) {
+  // the source level of cavity c this launch: its level at batch creation, flipped on odd
+  // launches
+  auto tile_of = [&](int tile) {
     const uint32_t e = tiles[tile];
-    const BatchCav& cv = cavs[tile_cav(e)];
+    const int c = tile_cav(e);
+    const BatchCav& cv = cavs[c];
     const int from = cv.cur ^ parity;
-    const uint32_t bar = bar0 + 8u * stage;
-    tma::mbar_expect_tx(bar, BYTES);
-    tma::load_3d(win0 + stage * BYTES, &cv.map, tile_x(e) * TX - XO, tile_y(e) * TY - 2,
-                 from * kPlanes, bar);
+    return pair::TmaTileDesc{&cv.map, &cv.map_out, from * kPlanes, (from ^ 1) * kPlanes,
+                             tile_x(e) * pair::kTX, tile_y(e) * pair::kTY, cv.L, cv.k,
+                             cv.level[from ^ 1], sh ^ ((uint32_t)c << 24)};
   };
-
-  int tile = blockIdx.x;
-  if (t == 0 && tile < n_tiles) issue(tile, 0);
-  for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
-    const int stage = it & 1;
-    const int next = tile + gridDim.x;
-    if (t == 0 && next < n_tiles) {
-      tma::fence_proxy_async();
-      issue(next, stage ^ 1);
-    }
-    const bool ok = tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
-    const uint32_t e = tiles[tile];
-    const BatchCav& cv = cavs[tile_cav(e)];
-    const Layout L = cv.L;
-    const float inv_nx = cv.k.inv_nx;
-    const T* w = reinterpret_cast<const T*>(win_raw + stage * BYTES);
-    const int i0 = tile_x(e) * TX, j0 = tile_y(e) * TY;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool active = i < L.nx && j < L.ny;
-    const int gi = i0 + hx, gj = j0 + hy;
-    const bool ring = t < NRING && gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
-    float fw[kQ], fp[kQ], g[kQ];
-    if (active) {
-      pull_window<T, true>(w, L, i, j, tx + XO, ty + 2, fw, fp, g, inv_nx);
-      s_th[ty + 1][tx + 1] = sum9(g);
-      s_rp[ty + 1][tx + 1] = sum9(fp);
-    }
-    if (ring) {
-      float hw[kQ], hp[kQ], hg[kQ];
-      pull_window<T, false>(w, L, gi, gj, hx + XO, hy + 2, hw, hp, hg, inv_nx);
-      s_th[hy + 1][hx + 1] = sum9(hg);
-      s_rp[hy + 1][hx + 1] = sum9(hp);
-    }
-    if (!ok) s_abort = 1;
-    __syncthreads();
-    if (s_abort) {
-      if (t == 0) {
-        atomicOr(err, 1);
-        tma::mbar_wait(bar0 + 8u * stage, (it >> 1) & 1);
-        if (next < n_tiles) tma::mbar_wait(bar0 + 8u * (stage ^ 1), ((it + 1) >> 1) & 1);
-      }
-      return;
-    }
-    if (active) {
-      const float th = s_th[ty + 1][tx + 1], rp = s_rp[ty + 1][tx + 1];
-      const float thW = (i > 0) ? s_th[ty + 1][tx] : -th;
-      const float thE = (i + 1 < L.nx) ? s_th[ty + 1][tx + 2] : -th;
-      const float thS = (j > 0) ? s_th[ty][tx + 1] : th;
-      const float thN = (j + 1 < L.ny) ? s_th[ty + 2][tx + 1] : th;
-      const float rpW = (i > 0) ? s_rp[ty + 1][tx] : rp;
-      const float rpE = (i + 1 < L.nx) ? s_rp[ty + 1][tx + 2] : rp;
-      const float rpS = (j > 0) ? s_rp[ty][tx + 1] : rp;
-      const float rpN = (j + 1 < L.ny) ? s_rp[ty + 2][tx + 1] : rp;
-      const size_t o = (size_t)j * L.pitch + i;
-      T* dst = static_cast<T*>(cv.level[cv.cur ^ parity ^ 1]);
-      StoreSink<T, SR> out{dst + o, L.plane,
-                           SR ? mix32((uint32_t)o ^ sh ^ ((uint32_t)tile_cav(e) << 24)) : 0u};
-      collide<ALLF>(cv.k, L, out, i, j, fw, fp, g, thE, thW, thN, thS, rpE, rpW, rpN, rpS);
-    }
-    __syncthreads();
-  }
+  pair::tma_tile_loop<T, SR, ALLF, 2>(tile_of, n_tiles, err);
 }
 
 // Nusselt sums of every cavity: block c reduces cavity c (the same sums as nusselt_kernel).
@@ -202,8 +108,8 @@ cudaError_t launch_batch_t3(const BatchLaunch& b, int parity, uint32_t seed, cud
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3(b.grid);
-  cfg.blockDim = dim3(kTmaTX * kTmaTY);
-  cfg.dynamicSmemBytes = 2 * (size_t)TmaTile<T>::BYTES;
+  cfg.blockDim = dim3(pair::Threads<2>::value);
+  cfg.dynamicSmemBytes = pair::TmaPair<T, 2>::SMEM;
   return cudaLaunchKernelEx(&cfg, step_batch_kernel<T, SR, ALLF>,
                             (const BatchCav*)b.cavs, (const uint32_t*)b.tiles, b.n_tiles, parity,
                             seed, (const uint32_t*)b.epoch, b.err);
@@ -211,7 +117,7 @@ cudaError_t launch_batch_t3(const BatchLaunch& b, int parity, uint32_t seed, cud
 
 template <class T>
 cudaError_t launch_batch_t(const BatchLaunch& b, int parity, uint32_t seed, cudaStream_t st) {
-  const bool sr = b.sr && Elem<T>::kBytes == 2;
+  const bool sr = b.sr && sizeof(T) == 2;
   if (sr)
     return b.all_forces ? launch_batch_t3<T, true, true>(b, parity, seed, st)
                         : launch_batch_t3<T, true, false>(b, parity, seed, st);
@@ -221,7 +127,7 @@ cudaError_t launch_batch_t(const BatchLaunch& b, int parity, uint32_t seed, cuda
 
 template <class T>
 cudaError_t prepare_batch_t(int* per_sm) {
-  const size_t smem = 2 * (size_t)TmaTile<T>::BYTES;
+  const size_t smem = pair::TmaPair<T, 2>::SMEM;
   const void* fns[4] = {(const void*)step_batch_kernel<T, false, false>,
                         (const void*)step_batch_kernel<T, false, true>,
                         (const void*)step_batch_kernel<T, true, false>,
@@ -231,8 +137,10 @@ cudaError_t prepare_batch_t(int* per_sm) {
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_batch_kernel<T, false, true>,
-                                                       kTmaTX * kTmaTY, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_batch_kernel<T, true, true>,
+                                                    pair::Threads<2>::value, smem);
+  if (e == cudaSuccess && *per_sm > pair::MinBlocks<2>::value) *per_sm = pair::MinBlocks<2>::value;
+  return e;
 }
 }  // namespace
 

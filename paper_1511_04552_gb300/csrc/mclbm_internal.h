@@ -71,9 +71,11 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
-  int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles
+  int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles (node pairs per thread);
+                // 10, 12: the same with one node per thread
   int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
   bool sr;      // 16-bit storage: stochastic rounding (else round to nearest)
+  int vec;      // nodes per thread of the step kernels: 1 or 2 (0: chosen by lattice size)
 };
 StepConfig choose_step_config(int nx, int ny);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
@@ -120,7 +122,8 @@ cudaError_t launch_state_copy(const void* src, void* dst, const Layout& L, bool 
 // ---- batched stepping of many cavities (mclbm_batch.cu) ------------------------------------
 // One cavity of a batch as the batch kernel sees it (device memory, 64-byte aligned).
 struct BatchCav {  // aligned like its CUtensorMap member
-  CUtensorMap map;  // window loads of the cavity's two-level state
+  CUtensorMap map;      // window loads of the cavity's two-level state
+  CUtensorMap map_out;  // output tile stores (16-bit storage)
   void* level[2];   // the two state levels
   Layout L;
   StepConsts k;

@@ -223,20 +223,35 @@ def test_determinism():
     assert outs[0][1:] == outs[1][1:]
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 32), (130, 35), (200, 67), (100, 100)])
-def test_step_variants_bitwise_identical(nx, ny, monkeypatch):
+@pytest.mark.parametrize("nx,ny", [(64, 32), (130, 35), (200, 67), (100, 100), (37, 29)])
+@pytest.mark.parametrize("storage", [0, 1])
+def test_step_variants_bitwise_identical(nx, ny, storage, monkeypatch):
     """The tile kernel and the TMA-staged persistent kernel organise the same per-node
-    arithmetic differently; their states after 300 steps are identical bit for bit."""
+    arithmetic differently; with the same number of nodes per thread their states after 300
+    steps are identical bit for bit (16-bit storage with round to nearest, so that the random
+    rounding streams do not enter). One node per thread against two (packed FP32x2
+    arithmetic): the all-forces build rounds a few operations differently on odd-width
+    lattices (a 1-ulp difference first seen in the drag's frozen-force term at the centre
+    column), so there the two widths agree to a relative L2 of 1e-6 per plane group in FP32,
+    and to 1e-3 with 16-bit storage, where one FP32 ulp can flip a stored rounding."""
     import torch
     import paper_1511_04552_gb300 as m
     states = {}
     for name in ("tile", "tma"):
-        monkeypatch.setenv("MCLBM_STEP_VARIANT", name)
-        cav = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9).init()
-        cav.step(300)
-        states[name] = cav.state_get()
-        cav.nusselt()  # raises MCLBM_ETIMEOUT if a bounded wait gave up
-    assert torch.equal(states["tma"], states["tile"])
+        for vec in ("1", "2"):
+            monkeypatch.setenv("MCLBM_STEP_VARIANT", name)
+            monkeypatch.setenv("MCLBM_STEP_VEC", vec)
+            cav = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9, storage=storage, rounding=1).init()
+            cav.step(300)
+            states[name + vec] = cav.state_get()
+            cav.nusselt()  # raises MCLBM_ETIMEOUT if a bounded wait gave up
+    assert torch.equal(states["tma1"], states["tile1"])
+    assert torch.equal(states["tma2"], states["tile2"])
+    a, b = states["tile1"].double(), states["tile2"].double()
+    for g in range(3):  # f^w, f^p, g deviations
+        den = a[9 * g:9 * g + 9].norm()
+        tol = 1e-6 if storage == 0 else 1e-3
+        assert (a[9 * g:9 * g + 9] - b[9 * g:9 * g + 9]).norm() <= tol * den, g
 
 
 def test_warm_init_with_density_matches_oracle():
