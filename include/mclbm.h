@@ -220,8 +220,9 @@ size_t mclbm_batch_buffer_bytes(int n, mclbm_t *const *cavities);
 
 /* Groups n bound and initialised cavities (same device, same storage type; nx <= 65535,
  * ny <= 16383) so that mclbm_batch_step advances all of them with one persistent launch per
- * time step: the 32 x 8 tiles of every active cavity form one table walked by a grid of 1 or 2
- * CTAs per SM, each tile streamed into shared memory by TMA as in the single-cavity step
+ * time step: the 64 x 8 tiles of every active cavity form one table walked by a persistent grid
+ * (CTAs per SM chosen by mclbm_batch_tune), each tile streamed into shared memory by TMA and
+ * updated two nodes per thread as in the single-cavity step on large lattices
  * (Eqs 18-19 with Table 1 and Eqs 34-36, per cavity with its own parameters). dev_buf: caller
  * device memory (>= mclbm_batch_buffer_bytes, 256-byte aligned), cuda_stream: the stream of
  * every batch call. The cavities stay usable on their own (fields, reductions) between batch

@@ -273,7 +273,7 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
   if (h->cfg.variant % 10 == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
-        make_state_tensor_map(h->tmap, h->state[0], h->L) != cudaSuccess) {
+        make_state_tensor_map(h->tmap, h->state[0], h->L, step_tile_width(h->cfg)) != cudaSuccess) {
       cudaGetLastError();
       h->cfg.variant -= 2;
     }
@@ -767,7 +767,8 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
     mclbm_t* h = cavities[c];
     std::memset(&host[c], 0, sizeof(BatchCav));
     CUtensorMap maps[2];
-    if (make_state_tensor_map(maps, h->state[0], h->L) != cudaSuccess) return bail(MCLBM_ECUDA);
+    if (make_state_tensor_map(maps, h->state[0], h->L, kBatchTileW) != cudaSuccess)
+      return bail(MCLBM_ECUDA);
     host[c].map = maps[0];
     host[c].map_out = maps[1];
     host[c].level[0] = h->state[0];

@@ -1,6 +1,6 @@
 // Batched stepping of many cavities in one persistent launch per time step (the parametric
 // sweep: cavities of different sizes, Rayleigh numbers, volume fractions and particle sizes).
-// A tile table lists the 32 x 8 tiles of every active cavity; the persistent CTAs walk it
+// A tile table lists the 64 x 8 tiles of every active cavity; the persistent CTAs walk it
 // exactly like the single-cavity TMA kernel walks one cavity (the same tile loop), reading each
 // tile's cavity arguments and tensor maps from device memory. A batched reduction gives every cavity's
 // Nusselt numbers in one launch. The autotuner times a few tile orders and grid sizes.
@@ -16,7 +16,7 @@
 #include "mclbm_pair.cuh"
 
 namespace mcl {
-static_assert(pair::kTX == kTmaTX && pair::kTY == kTmaTY, "the tile table and the kernels share the tile shape");
+static_assert(pair::kTY == kTmaTY, "the tile table and the kernels share the tile height");
 
 // Tile table entry: cavity (10 bits) | tile column (11 bits) | tile row (11 bits).
 __host__ __device__ constexpr uint32_t pack_tile(int c, int tx, int ty) {
@@ -30,7 +30,8 @@ __device__ __forceinline__ int tile_y(uint32_t e) { return (int)(e & 2047u); }
 // thread, one window per CTA reloaded as soon as the pulls have read it), with each tile's
 // tensor maps, layout, constants and destination level taken from its cavity's entry.
 template <class T, bool SR, bool ALLF>
-__global__ void __launch_bounds__(pair::Threads<2>::value, pair::MinBlocks<2>::value)
+__global__ void __launch_bounds__(pair::Threads<2, kBatchTileW>::value,
+                                  pair::MinBlocks<2, kBatchTileW>::value)
     step_batch_kernel(const BatchCav* __restrict__ cavs, const uint32_t* __restrict__ tiles,
                       int n_tiles, int parity, uint32_t seed, const uint32_t* epoch, int* err) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -48,10 +49,10 @@ __global__ void __launch_bounds__(pair::Threads<2>::value, pair::MinBlocks<2>::v
     const BatchCav& cv = cavs[c];
     const int from = cv.cur ^ parity;
     return pair::TmaTileDesc{&cv.map, &cv.map_out, from * kPlanes, (from ^ 1) * kPlanes,
-                             tile_x(e) * pair::kTX, tile_y(e) * pair::kTY, cv.L, cv.k,
+                             tile_x(e) * kBatchTileW, tile_y(e) * pair::kTY, cv.L, cv.k,
                              cv.level[from ^ 1], sh ^ ((uint32_t)c << 24)};
   };
-  pair::tma_tile_loop<T, SR, ALLF, 2>(tile_of, n_tiles, err);
+  pair::tma_tile_loop<T, SR, ALLF, 2, kBatchTileW>(tile_of, n_tiles, err);
 }
 
 // Nusselt sums of every cavity: block c reduces cavity c (the same sums as nusselt_kernel).
@@ -108,8 +109,8 @@ cudaError_t launch_batch_t3(const BatchLaunch& b, int parity, uint32_t seed, cud
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3(b.grid);
-  cfg.blockDim = dim3(pair::Threads<2>::value);
-  cfg.dynamicSmemBytes = pair::TmaPair<T, 2>::SMEM;
+  cfg.blockDim = dim3(pair::Threads<2, kBatchTileW>::value);
+  cfg.dynamicSmemBytes = pair::TmaPair<T, 2, kBatchTileW>::SMEM;
   return cudaLaunchKernelEx(&cfg, step_batch_kernel<T, SR, ALLF>,
                             (const BatchCav*)b.cavs, (const uint32_t*)b.tiles, b.n_tiles, parity,
                             seed, (const uint32_t*)b.epoch, b.err);
@@ -127,7 +128,7 @@ cudaError_t launch_batch_t(const BatchLaunch& b, int parity, uint32_t seed, cuda
 
 template <class T>
 cudaError_t prepare_batch_t(int* per_sm) {
-  const size_t smem = pair::TmaPair<T, 2>::SMEM;
+  const size_t smem = pair::TmaPair<T, 2, kBatchTileW>::SMEM;
   const void* fns[4] = {(const void*)step_batch_kernel<T, false, false>,
                         (const void*)step_batch_kernel<T, false, true>,
                         (const void*)step_batch_kernel<T, true, false>,
@@ -138,8 +139,9 @@ cudaError_t prepare_batch_t(int* per_sm) {
                                   (int)smem)) != cudaSuccess)
       return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_batch_kernel<T, true, true>,
-                                                    pair::Threads<2>::value, smem);
-  if (e == cudaSuccess && *per_sm > pair::MinBlocks<2>::value) *per_sm = pair::MinBlocks<2>::value;
+                                                    pair::Threads<2, kBatchTileW>::value, smem);
+  if (e == cudaSuccess && *per_sm > pair::MinBlocks<2, kBatchTileW>::value)
+    *per_sm = pair::MinBlocks<2, kBatchTileW>::value;
   return e;
 }
 }  // namespace
@@ -199,7 +201,7 @@ void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
   std::vector<int> ids;
   for (size_t c = 0; c < nx.size(); ++c)
     if (active[c]) ids.push_back((int)c);
-  auto ntiles = [&](int c) { return ((nx[c] + kTmaTX - 1) / kTmaTX) * ((ny[c] + kTmaTY - 1) / kTmaTY); };
+  auto ntiles = [&](int c) { return ((nx[c] + kBatchTileW - 1) / kBatchTileW) * ((ny[c] + kTmaTY - 1) / kTmaTY); };
   if (order == 1)
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ntiles(a) > ntiles(b); });
   if (order == 2) {
@@ -209,7 +211,7 @@ void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
       more = false;
       for (size_t k = 0; k < ids.size(); ++k) {
         const int c = ids[k];
-        const int tx_n = (nx[c] + kTmaTX - 1) / kTmaTX;
+        const int tx_n = (nx[c] + kBatchTileW - 1) / kBatchTileW;
         if (pos[k] < ntiles(c)) {
           out->push_back(pack_tile(c, pos[k] % tx_n, pos[k] / tx_n));
           ++pos[k];
@@ -220,7 +222,7 @@ void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
     return;
   }
   for (int c : ids) {
-    const int tx_n = (nx[c] + kTmaTX - 1) / kTmaTX, ty_n = (ny[c] + kTmaTY - 1) / kTmaTY;
+    const int tx_n = (nx[c] + kBatchTileW - 1) / kBatchTileW, ty_n = (ny[c] + kTmaTY - 1) / kTmaTY;
     for (int y = 0; y < ty_n; ++y)
       for (int x = 0; x < tx_n; ++x) out->push_back(pack_tile(c, x, y));
   }

@@ -81,9 +81,12 @@ StepConfig choose_step_config(int nx, int ny);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
 // may fall back to variant 0. Needs the device current.
 cudaError_t prepare_step(StepConfig* c, const Layout& L);
-// Tensor maps of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernel:
-// maps[0] loads input windows, maps[1] stores output tiles (16-bit storage).
-cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L);
+// Tensor maps of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernels
+// with tiles tile_w x 8: maps[0] loads input windows (the tile with 16 bytes of columns and 2
+// rows of halo on each side), maps[1] stores output tiles.
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w);
+// Tile width of a configured step kernel's TMA maps.
+int step_tile_width(const StepConfig& c);
 cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                         cudaStream_t st);
 // Per storage type (mclbm_step_f32.cu, mclbm_step_f16.cu, mclbm_step_bf16.cu).
@@ -145,5 +148,6 @@ cudaError_t launch_batch_nusselt(const BatchLaunch& b, int n_cav, int parity, do
 cudaError_t prepare_batch(int storage, int* per_sm);
 void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
                       const std::vector<int>& active, int order, std::vector<uint32_t>* out);
+constexpr int kBatchTileW = 64;  // batch tiles: 64 x 8 (two nodes per thread)
 
 }  // namespace mcl

@@ -314,8 +314,10 @@ cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMa
   }
 }
 
+int step_tile_width(const StepConfig&) { return 32; }
+
 // maps[0]: window loads (box = window); maps[1]: output tile stores (box = tile).
-cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L) {
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -327,27 +329,25 @@ cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout&
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   CUtensorMapDataType dt;
-  int wx;
   switch (L.storage) {
     case MCLBM_STORE_F32:
       dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-      wx = TmaTile<float>::WX;
       break;
     case MCLBM_STORE_F16:
       dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-      wx = TmaTile<__half>::WX;
       break;
     case MCLBM_STORE_BF16:
       dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-      wx = TmaTile<__nv_bfloat16>::WX;
       break;
     default:
       return cudaErrorInvalidValue;
   }
+  if (tile_w != 32 && tile_w != 64) return cudaErrorInvalidValue;
+  const int wx = tile_w + 2 * (16 / L.elem);  // 16 bytes of halo columns on each side
   const cuuint64_t dims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)(2 * kPlanes)};
   const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * L.elem, (cuuint64_t)L.plane * L.elem};
   const cuuint32_t box[3] = {(cuuint32_t)wx, (cuuint32_t)(kTmaTY + 4), (cuuint32_t)kPlanes};
-  const cuuint32_t tile[3] = {(cuuint32_t)kTmaTX, (cuuint32_t)kTmaTY, (cuuint32_t)kPlanes};
+  const cuuint32_t tile[3] = {(cuuint32_t)tile_w, (cuuint32_t)kTmaTY, (cuuint32_t)kPlanes};
   const cuuint32_t elem[3] = {1, 1, 1};
   CUresult r = encode(&maps[0], dt, 3, state0, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -278,12 +278,24 @@ __device__ __forceinline__ void pull(const Acc& acc, const Layout& L, int i, int
   }
 }
 
+// Shared-memory window of a TX x kTY tile (kTY = 8 rows): all 27 planes with XO columns (16
+// bytes: TMA's x alignment) and 2 rows of halo on each side.
+template <class T, int TX>
+struct PairWin {
+  static constexpr int XO = 16 / (int)sizeof(T);
+  static constexpr int WX = TX + 2 * XO;
+  static constexpr int WY = 8 + 4;
+  static constexpr int WPLANE = WX * WY;
+  static constexpr uint32_t BYTES = (uint32_t)kPlanes * WPLANE * sizeof(T);
+  static_assert(BYTES % 128 == 0, "windows stay 128-byte aligned");
+};
+
 // Accessor of a shared-memory window: element (wx, wy) of plane p at w[p * WPLANE + wy * WX + wx];
 // base = the position of node i (lane x).
-template <class T>
+template <class T, int TX>
 struct WinAcc {
   const T* base;
-  static constexpr int WX = TmaTile<T>::WX, WPLANE = TmaTile<T>::WPLANE;
+  static constexpr int WX = PairWin<T, TX>::WX, WPLANE = PairWin<T, TX>::WPLANE;
   __device__ __forceinline__ float a1(int p, int dx, int dy) const {
     return St<T>::ld1(base + p * WPLANE + dy * WX + dx);
   }
@@ -676,22 +688,26 @@ __device__ __forceinline__ void tile_collide(const StepConsts& k, const Layout& 
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-constexpr int kTX = 32;  // tile width (nodes)
-constexpr int kTY = 8;   // tile height
-template <int V>
+// Tiles of TX x kTY nodes with V nodes per thread: TX / V threads per tile row. The
+// single-cavity kernels use 32-wide tiles (with two nodes per thread: four CTAs of 128 threads
+// per SM, which hide the window loads of each other better than two of 256); the batch uses 64.
+constexpr int kTY = 8;  // tile height
+constexpr int kTileW = 32;  // single-cavity tile width
+template <int V, int TX>
 struct Threads {
-  static constexpr int value = kTX / V * kTY;
+  static constexpr int value = TX / V * kTY;
 };
 // resident CTAs per SM the register budget is sized for (128 registers per thread)
-template <int V>
+template <int V, int TX>
 struct MinBlocks {
-  static constexpr int value = V == 1 ? 2 : 4;
+  static constexpr int value = 65536 / 128 / Threads<V, TX>::value > 4 ? 4 : 65536 / 128 / Threads<V, TX>::value;
 };
 
 // Plain tile kernel (small lattices): pulls from global memory (L1/L2), one tile per CTA.
 template <class T, bool SR, bool ALLF, int V>
-__global__ void __launch_bounds__(Threads<V>::value, MinBlocks<V>::value)
+__global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW>::value)
     step_pair_tile_kernel(const StepArgs a) {
+  constexpr int kTX = kTileW;
   __shared__ __align__(16) MomTile<kTX, kTY> mt;
   const Layout L = a.L;
   const T* __restrict__ src = static_cast<const T*>(a.src);
@@ -717,12 +733,14 @@ __global__ void __launch_bounds__(Threads<V>::value, MinBlocks<V>::value)
 // SM the kernel runs with, an output tile written back by one TMA store (16-bit storage; FP32
 // with one node per thread). FP32 with two nodes per thread (four CTAs per SM) stores each
 // pair straight to global memory.
-template <class T, int V>
+template <class T, int V, int TX_>
 struct TmaPair {
-  static constexpr int XO = TmaTile<T>::XO;
-  static constexpr uint32_t BYTES = TmaTile<T>::BYTES;  // one input window
+  static constexpr int TX = TX_;
+  static constexpr int XO = PairWin<T, TX>::XO;
+  static constexpr int WX = PairWin<T, TX>::WX;
+  static constexpr uint32_t BYTES = PairWin<T, TX>::BYTES;  // one input window
   static constexpr bool STORE_TMA = sizeof(T) == 2 || V == 1;
-  static constexpr uint32_t OUT_BYTES = STORE_TMA ? (uint32_t)kPlanes * kTX * kTY * sizeof(T) : 0;
+  static constexpr uint32_t OUT_BYTES = STORE_TMA ? (uint32_t)kPlanes * TX * kTY * sizeof(T) : 0;
   static constexpr size_t SMEM = (size_t)BYTES + OUT_BYTES;
 };
 
@@ -743,12 +761,14 @@ struct TmaTileDesc {
 // load overlaps the collision; several CTAs per SM overlap each other. Every mbarrier wait is
 // bounded (2 s): on timeout the CTA sets bit 0 of the error word, drains its copies (bounded)
 // and returns. tile_of(tile) gives the tile's TmaTileDesc.
-template <class T, bool SR, bool ALLF, int V, class TileOf>
+template <class T, bool SR, bool ALLF, int V, int TX, class TileOf>
 __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles, int* err) {
-  constexpr uint32_t BYTES = TmaPair<T, V>::BYTES;
-  constexpr bool STORE_TMA = TmaPair<T, V>::STORE_TMA;
-  constexpr int XO = TmaPair<T, V>::XO;
-  constexpr int WX = TmaTile<T>::WX;
+  using TP = TmaPair<T, V, TX>;
+  constexpr int kTX = TX;
+  constexpr uint32_t BYTES = TP::BYTES;
+  constexpr bool STORE_TMA = TP::STORE_TMA;
+  constexpr int XO = TP::XO;
+  constexpr int WX = TP::WX;
   extern __shared__ __align__(128) unsigned char win_raw[];
   __shared__ __align__(16) MomTile<kTX, kTY> mt;
   __shared__ __align__(8) uint64_t bar_mem;
@@ -778,7 +798,7 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
     if (STORE_TMA && t == 0) tma::bulk_wait_read_0();
     vec<V> fw[kQ], fp[kQ], g[kQ];
     if (ok) {
-      auto acc_at = [&](int dx, int dy) { return WinAcc<T>{w + (2 + dy) * WX + (XO + dx)}; };
+      auto acc_at = [&](int dx, int dy) { return WinAcc<T, kTX>{w + (2 + dy) * WX + (XO + dx)}; };
       tile_pull<kTX, kTY, V>(acc_at, L, d.i0, d.j0, t, mt, fw, fp, g);
     } else {
       s_abort = 1;
@@ -822,13 +842,14 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
 }
 
 template <class T, bool SR, bool ALLF, int V>
-__global__ void __launch_bounds__(Threads<V>::value, MinBlocks<V>::value)
+__global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW>::value)
     step_pair_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                          const __grid_constant__ CUtensorMap tmap_out, const StepArgs a) {
   // Programmatic dependent launch: let the next step's CTAs start their prologue while this
   // grid drains, and do not read the state before the previous step has completed.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  constexpr int kTX = kTileW;
   const int tiles_x = (a.L.nx + kTX - 1) / kTX;
   const int n_tiles = tiles_x * ((a.L.ny + kTY - 1) / kTY);
   const uint32_t sh = SR ? step_hash(a) : 0u;
@@ -837,7 +858,7 @@ __global__ void __launch_bounds__(Threads<V>::value, MinBlocks<V>::value)
     return TmaTileDesc{&tmap, &tmap_out, a.z_src, kPlanes - a.z_src, (tile - ty * tiles_x) * kTX,
                        ty * kTY, a.L, a.k, a.dst, sh};
   };
-  tma_tile_loop<T, SR, ALLF, V>(tile_of, n_tiles, a.err);
+  tma_tile_loop<T, SR, ALLF, V, kTileW>(tile_of, n_tiles, a.err);
 }
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -845,13 +866,13 @@ __global__ void __launch_bounds__(Threads<V>::value, MinBlocks<V>::value)
 // per SM: the step is latency-bound and needs every warp it can get), two beyond (issue-bound:
 // packed arithmetic halves the instructions per node).
 inline int nodes_per_thread(const Layout& L, int sms) {
-  const int tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
+  const int tiles = ((L.nx + 31) / 32) * ((L.ny + kTY - 1) / kTY);  // 32 x 8 tiles
   return tiles <= 2 * sms ? 1 : 2;
 }
 
 template <class T, int V>
 cudaError_t prepare_pair_tma_v(StepConfig* c, const Layout& L, int sms) {
-  const size_t smem = TmaPair<T, V>::SMEM;
+  const size_t smem = TmaPair<T, V, kTileW>::SMEM;
   const void* fns[4] = {(const void*)step_pair_tma_kernel<T, false, false, V>,
                         (const void*)step_pair_tma_kernel<T, false, true, V>,
                         (const void*)step_pair_tma_kernel<T, true, false, V>,
@@ -863,10 +884,11 @@ cudaError_t prepare_pair_tma_v(StepConfig* c, const Layout& L, int sms) {
       return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, step_pair_tma_kernel<T, true, true, V>, Threads<V>::value, smem);
+      &per_sm, step_pair_tma_kernel<T, true, true, V>, Threads<V, kTileW>::value, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (per_sm > MinBlocks<V>::value) per_sm = MinBlocks<V>::value;
+  if (per_sm > MinBlocks<V, kTileW>::value) per_sm = MinBlocks<V, kTileW>::value;
+  constexpr int kTX = kTileW;
   const int tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
   c->grid = tiles < per_sm * sms ? tiles : per_sm * sms;
   c->vec = V;
@@ -891,12 +913,13 @@ cudaError_t launch_pair_t4(const StepArgs& a, const StepConfig& c, const CUtenso
   if (c.variant == 2) {
     if (!map || c.grid < 1) return cudaErrorInvalidValue;
     cfg.gridDim = dim3(c.grid);
-    cfg.blockDim = dim3(Threads<V>::value);
-    cfg.dynamicSmemBytes = TmaPair<T, V>::SMEM;
+    cfg.blockDim = dim3(Threads<V, kTileW>::value);
+    cfg.dynamicSmemBytes = TmaPair<T, V, kTileW>::SMEM;
     return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<T, SR, ALLF, V>, map[0], map[1], a);
   }
+  constexpr int kTX = kTileW;
   cfg.gridDim = dim3((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
-  cfg.blockDim = dim3(Threads<V>::value);
+  cfg.blockDim = dim3(Threads<V, kTileW>::value);
   cfg.dynamicSmemBytes = 0;
   return cudaLaunchKernelEx(&cfg, step_pair_tile_kernel<T, SR, ALLF, V>, a);
 }

@@ -1,6 +1,9 @@
 """16-bit population storage (FP16 / BF16 holding 2^12 x the deviations, FP32 arithmetic):
 exact round trips, identical results from both step kernels, and accuracy against the FP64
 oracle within the reduced-storage target (mean Nusselt number within 0.5 %)."""
+import os
+
+import numpy as np
 import pytest
 
 import workloads
@@ -75,24 +78,47 @@ def test_accuracy_against_fp64_oracle(storage, nu_tol, u_tol, th_tol):
     assert abs(mw - rw) <= 1e-4 * rw and abs(mp - rp) <= 1e-3 * rp
 
 
-@pytest.mark.parametrize("storage,nu_tol", [("f16", 5e-3), ("bf16", 3e-2)])
-def test_per_result_error_at_1024(storage, nu_tol):
-    """The precision configuration: 1024^2, Ra 1e6, phi 2 %, 50 nm, 20 000 steps from rest. The
-    reference is the FP32-storage run (within 1e-5 of the FP64 oracle by the parity tests; the
-    oracle itself would need hours here). Errors per result: mean hot-wall Nu, max |u|, and the
-    relative L2 of the concentration's deviation from its initial value."""
+GOLDEN_1024 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "oracle_cavity1024_20000.npz")
+
+
+# Measured on GB300 (per result: Nu, max |u|, phi - phi0, velocity fields):
+#   FP32 3.9e-7, 2.0e-5, 1.8e-4, 2.2e-5; FP16 2.1e-4, 2.8e-4, 7.5e-3, 2.8e-4;
+#   BF16 9.0e-4, 5.5e-3, 6.2e-2, 2.3e-3.
+# FP32: Nu within the parity bar, the velocities at 2e-5 (FP32 rounding accumulated over 20 000
+# steps of a 1024^2 lattice; the 32^2 and 64^2 parity cases stay below 1e-5), and phi - phi0 has
+# an RMS of 5e-4 of phi0 here, which a float32 phi (the fields' and the stored sample's type)
+# resolves only to about 2e-4. FP16 meets the
+# reduced-storage target (mean Nu within 0.5 %); BF16 its measured errors with margin.
+@pytest.mark.parametrize("storage,nu_tol,u_tol,phi_tol", [("f32", 1e-5, 5e-5, 5e-4),
+                                                          ("f16", 5e-3, 1e-2, 5e-2),
+                                                          ("bf16", 3e-2, 5e-2, 3e-1)])
+def test_per_result_error_at_1024(storage, nu_tol, u_tol, phi_tol):
+    """The precision configuration: 1024^2, Ra 1e6, phi 2 %, 50 nm, 20 000 steps from rest, each
+    storage type against the FP64 oracle's run of the same case (stored by
+    tests/golden/make_oracle_runs.py, which calls only the oracle). Errors per result: the mean
+    hot-wall Nusselt number, the maximum speed |u|, and the relative L2 of the concentration's
+    deviation from its initial value phi - phi0 (on every 4th row and column, the oracle's stored
+    sample), with the velocity fields on the same sample."""
     import paper_1511_04552_gb300 as m
+    ref = np.load(GOLDEN_1024)
     w = workloads.CAVITY_1024
-    ref = m.Cavity(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"]).init().step(20000)
-    cav = _cav(w["nx"], w["ny"], w["Ra"], w["phi"], w["d_p"], storage).init().step(20000)
-    fr, fc = ref.fields(m.UX | m.UY | m.PHI), cav.fields(m.UX | m.UY | m.PHI)
-    nu_r, nu_c = ref.nusselt()[0], cav.nusselt()[0]
-    umax_r = float((fr[0] ** 2 + fr[1] ** 2).sqrt().max())
-    umax_c = float((fc[0] ** 2 + fc[1] ** 2).sqrt().max())
-    dphi_r, dphi_c = (fr[2] - w["phi"]).double(), (fc[2] - w["phi"]).double()
-    e_nu = abs(nu_c - nu_r) / nu_r
-    e_u = abs(umax_c - umax_r) / umax_r
-    e_phi = float((dphi_c - dphi_r).norm() / dphi_r.norm())
-    print("%s at 1024^2: Nu %.2e, max|u| %.2e, phi deviation L2 %.2e" % (storage, e_nu, e_u, e_phi))
+    assert str(ref["workload"]) == w["name"] and int(ref["steps"]) == 20000
+    store = {"f32": 0, "f16": 1, "bf16": 2}[storage]
+    cav = m.Cavity(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"], storage=store)
+    cav.init().step(20000)
+    f = cav.fields(m.UX | m.UY | m.PHI).cpu().numpy().astype(np.float64)
+    nu = cav.nusselt()[0]
+    k = int(ref["sample"])
+    ux, uy, phi = f[0][::k, ::k], f[1][::k, ::k], f[2][::k, ::k]
+    e_nu = abs(nu - float(ref["nu_hot"])) / float(ref["nu_hot"])
+    umax = float(np.sqrt(f[0] ** 2 + f[1] ** 2).max())
+    e_u = abs(umax - float(ref["umax"])) / float(ref["umax"])
+    dphi_ref = ref["phi"].astype(np.float64) - w["phi"]
+    e_phi = P.rel_l2(phi - w["phi"], dphi_ref)
+    e_ux, e_uy = P.rel_l2(ux, ref["ux"]), P.rel_l2(uy, ref["uy"])
+    print("%s at 1024^2 against FP64: Nu %.2e, max|u| %.2e, phi deviation L2 %.2e, ux %.2e, uy %.2e"
+          % (storage, e_nu, e_u, e_phi, e_ux, e_uy))
     assert e_nu <= nu_tol
-    assert e_u <= 10 * nu_tol
+    assert e_u <= u_tol and e_ux <= u_tol and e_uy <= u_tol
+    assert e_phi <= phi_tol
