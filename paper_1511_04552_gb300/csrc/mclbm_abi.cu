@@ -271,11 +271,11 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   // kernel if the device cannot run it
   h->cfg = choose_step_config(h->nx, h->ny);
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
-  if (h->cfg.variant % 10 == 2) {
+  if (h->cfg.variant == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
         make_state_tensor_map(h->tmap, h->state[0], h->L, step_tile_width(h->cfg)) != cudaSuccess) {
       cudaGetLastError();
-      h->cfg.variant -= 2;
+      h->cfg.variant = 0;
     }
   }
   CK(h, cudaMemsetAsync(h->err_dev, 0, 2 * sizeof(int), h->stream));

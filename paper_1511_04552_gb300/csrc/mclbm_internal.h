@@ -71,8 +71,7 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
 
 // Kernel launchers (mclbm_kernels.cu). All enqueue on `st` and return the launch error.
 struct StepConfig {
-  int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles (node pairs per thread);
-                // 10, 12: the same with one node per thread
+  int variant;  // 0: tile kernel; 2: TMA-staged persistent tiles
   int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
   bool sr;      // 16-bit storage: stochastic rounding (else round to nearest)
   int vec;      // nodes per thread of the step kernels: 1 or 2 (0: chosen by lattice size)

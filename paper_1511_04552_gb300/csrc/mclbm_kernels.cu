@@ -271,13 +271,10 @@ StepConfig choose_step_config(int nx, int ny) {
   StepConfig c;
   // default: TMA-staged tiles for lattices with a few tiles per SM, the plain tile kernel below.
   // MCLBM_STEP_VARIANT = tile | tma overrides (diagnostics and comparisons).
-  // tile_v1 | tma_v1 select the one-node-per-thread kernels (10, 12) for comparisons.
   c.variant = (nx >= 64 && ny >= 32) ? 2 : 0;
   const char* v = std::getenv("MCLBM_STEP_VARIANT");
   if (v && std::strcmp(v, "tile") == 0) c.variant = 0;
   if (v && std::strcmp(v, "tma") == 0) c.variant = 2;
-  if (v && std::strcmp(v, "tile_v1") == 0) c.variant = 10;
-  if (v && std::strcmp(v, "tma_v1") == 0) c.variant = 12;
   c.grid = 0;
   c.sr = true;
   // MCLBM_STEP_VEC = 1 | 2 forces the nodes per thread (comparisons; default by lattice size)
@@ -287,7 +284,7 @@ StepConfig choose_step_config(int nx, int ny) {
 }
 
 cudaError_t prepare_step(StepConfig* c, const Layout& L) {
-  if (c->variant % 10 != 2) return cudaSuccess;
+  if (c->variant != 2) return cudaSuccess;
   switch (L.storage) {
     case MCLBM_STORE_F32:
       return prepare_tma_f32(c, L);

@@ -6,16 +6,11 @@ namespace mcl {
 
 cudaError_t launch_step_f16(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                            cudaStream_t st) {
-  if (c.variant >= 10) {  // the one-node-per-thread kernels (comparisons)
-    StepConfig c1 = c;
-    c1.variant -= 10;
-    return launch_step_t<__half>(a, c1, map, st);
-  }
   return pair::launch_pair_t<__half>(a, c, map, st);
 }
 
 cudaError_t prepare_tma_f16(StepConfig* c, const Layout& L) {
-  return c->variant >= 10 ? prepare_tma_t<__half>(c, L) : pair::prepare_pair_tma_t<__half>(c, L);
+  return pair::prepare_pair_tma_t<__half>(c, L);
 }
 
 }  // namespace mcl
