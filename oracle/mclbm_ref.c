@@ -44,6 +44,13 @@
  *     at the isothermal walls and theta_ghost = theta at the adiabatic walls;
  *   - Nu: mean over the hot wall of the second-order one-sided wall gradient, times k_ns/k_f,
  *     normalised by the hot-cold distance L = nx.
+ *   - the two-thermal-set variant (thermal_sets = 2, Eq 19 for both components): g^w and g^p
+ *     stream with the same wall rules, each relaxes with its own time (tau_theta^w of Eq 22's
+ *     thermal twin, tau_theta^p of Eq 24 at the initial fractions) towards the equilibrium at
+ *     the mixture temperature of Eq 33, theta^ns = (rho^w theta^w + r rho^p theta^p) /
+ *     (rho^w + r rho^p), r = C_p,p / C_p,f (the garbled weights of Eq 33 read as the
+ *     components' heat capacities), just as both f^sigma relax at the mixture velocity of
+ *     Eq 32; theta^ns drives buoyancy, the gradients and Nu.
  *
  * Parity pins (tests/test_oracle_*.py): equilibrium moments, streaming permutation and
  * displacement, exact mass conservation, the phi = 0 limit against an independent textbook
@@ -66,7 +73,6 @@
 #endif
 
 #define NQ 9
-#define NPLANES 27
 #define T_HOT 0.5
 #define T_COLD (-0.5)
 
@@ -93,16 +99,19 @@ static int mirror_y(int q) {
   return -1;
 }
 
-enum { M_RHOW, M_RHOP, M_MWX, M_MWY, M_MPX, M_MPY, M_THETA, NMOM };
+/* M_THETA: the (mixture) temperature; M_THW, M_THP: the two sets' own (= M_THETA with one) */
+enum { M_RHOW, M_RHOP, M_MWX, M_MWY, M_MPX, M_MPY, M_THETA, M_THW, M_THP, NMOM };
 
 struct ref_solver {
   int nx, ny;
   double Ra, Pr, phi0, d_p;
   ref_props pr;
   ref_consts c;
-  double *st[2]; /* [27][ny][nx] post-collision populations, two time levels */
+  int nsets;     /* population sets: 3 (f^w, f^p, g) or 4 (f^w, f^p, g^w, g^p) */
+  int np;        /* planes: 9 nsets */
+  double *st[2]; /* [np][ny][nx] post-collision populations, two time levels */
   int cur;
-  double *post; /* [27][ny][nx] post-stream populations of the step in progress */
+  double *post; /* [np][ny][nx] post-stream populations of the step in progress */
   double *mom;  /* [NMOM][ny][nx] moments of the post-stream populations */
   double *snap; /* [4][ny][nx] ux, uy, theta, phi at the last residual check */
   int64_t steps, snap_step;
@@ -147,6 +156,8 @@ void mclbm_ref_props_default(ref_props *p) {
   p->force_mask = REF_F_ALL;
   p->periodic_x = 0;
   p->body_fx = 0.0;
+  p->thermal_sets = 1;
+  p->tau_tp_override = 0.0;
 }
 
 /* Create-time constants: lattice scales, Eqs 7-11 at the initial phi, Eqs 22-24, SI scales. */
@@ -187,6 +198,7 @@ static int derive(ref_t *h) {
     c->tau_p = c->tau_w;
     c->tau_tp = c->tau_tw;
   }
+  if (p->tau_tp_override > 0.0) c->tau_tp = p->tau_tp_override;
   /* SI scales: physical height from Ra of the base fluid, then lattice spacing and time step */
   {
     const double nu_f = p->mu_f / p->rho_f, alpha_f = nu_f / h->Pr;
@@ -235,7 +247,7 @@ int mclbm_ref_create(int nx, int ny, double Ra, double Pr, double phi, double d_
   if (!(p.rho_f > 0) || !(p.cp_f > 0) || !(p.k_f > 0) || !(p.beta_f > 0) || !(p.mu_f > 0) ||
       !(p.rho_p > 0) || !(p.cp_p > 0) || !(p.k_p > 0) || !(p.beta_p >= 0) || !(p.T0 > 0) ||
       !(p.dT > 0) || !(p.g > 0) || !(p.l_f > 0) || !(p.Ma > 0 && p.Ma <= 0.5) ||
-      (p.force_mask & ~REF_F_ALL))
+      (p.force_mask & ~REF_F_ALL) || (p.thermal_sets != 1 && p.thermal_sets != 2))
     return REF_EPARAM;
   ref_t *h = (ref_t *)calloc(1, sizeof(ref_t));
   if (!h) return REF_ENOMEM;
@@ -246,15 +258,17 @@ int mclbm_ref_create(int nx, int ny, double Ra, double Pr, double phi, double d_
   h->phi0 = phi;
   h->d_p = d_p;
   h->pr = p;
+  h->nsets = 2 + p.thermal_sets;
+  h->np = NQ * h->nsets;
   int rc = derive(h);
   if (rc) {
     free(h);
     return rc;
   }
   const size_t n = (size_t)nx * ny;
-  h->st[0] = (double *)calloc(NPLANES * n, sizeof(double));
-  h->st[1] = (double *)calloc(NPLANES * n, sizeof(double));
-  h->post = (double *)calloc(NPLANES * n, sizeof(double));
+  h->st[0] = (double *)calloc((size_t)h->np * n, sizeof(double));
+  h->st[1] = (double *)calloc((size_t)h->np * n, sizeof(double));
+  h->post = (double *)calloc((size_t)h->np * n, sizeof(double));
   h->mom = (double *)calloc(NMOM * n, sizeof(double));
   h->snap = (double *)calloc(4 * n, sizeof(double));
   if (!h->st[0] || !h->st[1] || !h->post || !h->mom || !h->snap) {
@@ -309,9 +323,9 @@ static double pull(const ref_t *h, const double *st, int s, int q, int i, int j)
   if (s < 2) return AT(st, s * NQ + opposite(q), i, j);
   if (out_x) {
     const double Tw = (si < 0) ? T_HOT : T_COLD;
-    return -AT(st, 2 * NQ + opposite(q), i, j) + 2.0 * W[q] * Tw;
+    return -AT(st, s * NQ + opposite(q), i, j) + 2.0 * W[q] * Tw;
   }
-  return AT(st, 2 * NQ + mirror_y(q), si, j);
+  return AT(st, s * NQ + mirror_y(q), si, j);
 }
 
 static void stream_all(ref_t *h) {
@@ -319,8 +333,16 @@ static void stream_all(ref_t *h) {
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < h->ny; ++j)
     for (int i = 0; i < h->nx; ++i)
-      for (int s = 0; s < 3; ++s)
+      for (int s = 0; s < h->nsets; ++s)
         for (int q = 0; q < NQ; ++q) AT(h->post, s * NQ + q, i, j) = pull(h, st, s, q, i, j);
+}
+
+/* Eq 33 (two thermal sets): the enthalpy-weighted mixture temperature, with the partial
+ * densities (normalised by rho_f) times the specific heats as the components' heat capacities. */
+static double mixture_theta(const ref_t *h, double rho_w, double rho_p, double th_w,
+                            double th_p) {
+  const double r = h->pr.cp_p / h->pr.cp_f;
+  return (rho_w * th_w + r * rho_p * th_p) / (rho_w + r * rho_p);
 }
 
 /* Step 2: moments of the post-stream populations (Eqs 29-31). */
@@ -328,7 +350,7 @@ static void moments_all(ref_t *h) {
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < h->ny; ++j)
     for (int i = 0; i < h->nx; ++i) {
-      double rw = 0, rp = 0, mwx = 0, mwy = 0, mpx = 0, mpy = 0, th = 0;
+      double rw = 0, rp = 0, mwx = 0, mwy = 0, mpx = 0, mpy = 0, th = 0, thp = 0;
       for (int q = 0; q < NQ; ++q) {
         const double fw = AT(h->post, q, i, j), fp = AT(h->post, NQ + q, i, j);
         rw += fw;
@@ -338,6 +360,7 @@ static void moments_all(ref_t *h) {
         mpx += fp * EX[q];
         mpy += fp * EY[q];
         th += AT(h->post, 2 * NQ + q, i, j);
+        if (h->nsets == 4) thp += AT(h->post, 3 * NQ + q, i, j);
       }
       AT(h->mom, M_RHOW, i, j) = rw;
       AT(h->mom, M_RHOP, i, j) = rp;
@@ -345,7 +368,9 @@ static void moments_all(ref_t *h) {
       AT(h->mom, M_MWY, i, j) = mwy;
       AT(h->mom, M_MPX, i, j) = mpx;
       AT(h->mom, M_MPY, i, j) = mpy;
-      AT(h->mom, M_THETA, i, j) = th;
+      AT(h->mom, M_THW, i, j) = th;
+      AT(h->mom, M_THP, i, j) = h->nsets == 4 ? thp : th;
+      AT(h->mom, M_THETA, i, j) = h->nsets == 4 ? mixture_theta(h, rw, rp, th, thp) : th;
     }
 }
 
@@ -531,7 +556,13 @@ static void collide_node(ref_t *h, const ref_terms *t, int i, int j, double *dst
     const double Sp = 3.0 * W[q] * (EX[q] * t->F_p[0] + EY[q] * t->F_p[1]);
     AT(dst, q, i, j) = fw - (fw - eqw[q]) / c->tau_w + Sw;
     AT(dst, NQ + q, i, j) = fp - (fp - eqp[q]) / c->tau_p + Sp;
-    AT(dst, 2 * NQ + q, i, j) = g - (g - eqg[q]) / t->tau_theta;
+    if (h->nsets == 3) {
+      AT(dst, 2 * NQ + q, i, j) = g - (g - eqg[q]) / t->tau_theta;
+    } else { /* Eq 19 per component, both towards the mixture temperature (Eqs 27, 33) */
+      const double gp = AT(h->post, 3 * NQ + q, i, j);
+      AT(dst, 2 * NQ + q, i, j) = g - (g - eqg[q]) / c->tau_tw;
+      AT(dst, 3 * NQ + q, i, j) = gp - (gp - eqg[q]) / c->tau_tp;
+    }
   }
 }
 
@@ -564,7 +595,8 @@ int mclbm_ref_init(ref_t *h, int mode, const double *warm) {
       mclbm_ref_equilibrium(ph * h->pr.rho_p / h->pr.rho_f, ux, uy, e);
       for (int q = 0; q < NQ; ++q) AT(st, NQ + q, i, j) = e[q];
       mclbm_ref_equilibrium(th, ux, uy, e);
-      for (int q = 0; q < NQ; ++q) AT(st, 2 * NQ + q, i, j) = e[q];
+      for (int s = 2; s < h->nsets; ++s)
+        for (int q = 0; q < NQ; ++q) AT(st, s * NQ + q, i, j) = e[q];
     }
   h->cur = 0;
   h->steps = 0;
@@ -598,7 +630,7 @@ int mclbm_ref_stream_only(ref_t *h) {
   if (!h) return REF_EINVAL;
   if (!h->ready) return REF_ESTATE;
   stream_all(h);
-  memcpy(h->st[1 - h->cur], h->post, sizeof(double) * NPLANES * (size_t)h->nx * h->ny);
+  memcpy(h->st[1 - h->cur], h->post, sizeof(double) * h->np * (size_t)h->nx * h->ny);
   h->cur = 1 - h->cur;
   return REF_OK;
 }
@@ -614,13 +646,13 @@ int mclbm_ref_node_terms(ref_t *h, int i, int j, ref_terms *out) {
 
 /* Moments of the post-stream state: the fields the next step starts from. */
 int mclbm_ref_fields(ref_t *h, uint32_t which, double *out) {
-  if (!h || !out || !which || (which & ~0xFFu)) return REF_EINVAL;
+  if (!h || !out || !which || (which & ~0x3FFu)) return REF_EINVAL;
   if (!h->ready) return REF_ESTATE;
   stream_all(h);
   moments_all(h);
   const size_t n = (size_t)h->nx * h->ny;
   double *o = out;
-  for (int bit = 0; bit < 8; ++bit) {
+  for (int bit = 0; bit < 10; ++bit) {
     if (!(which & (1u << bit))) continue;
     for (int j = 0; j < h->ny; ++j)
       for (int i = 0; i < h->nx; ++i) {
@@ -637,6 +669,8 @@ int mclbm_ref_fields(ref_t *h, uint32_t which, double *out) {
           case REF_RHO_P: v = rp; break;
           case REF_UPX: v = rp > 1e-30 ? mpx / rp : mwx / rw; break;
           case REF_UPY: v = rp > 1e-30 ? mpy / rp : mwy / rw; break;
+          case REF_THETA_W: v = AT(h->mom, M_THW, i, j); break;
+          case REF_THETA_P: v = AT(h->mom, M_THP, i, j); break;
         }
         o[(size_t)j * h->nx + i] = v;
       }
@@ -727,13 +761,13 @@ int mclbm_ref_residual(ref_t *h, double *r) {
 int mclbm_ref_get_state(const ref_t *h, double *out) {
   if (!h || !out) return REF_EINVAL;
   if (!h->ready) return REF_ESTATE;
-  memcpy(out, h->st[h->cur], sizeof(double) * NPLANES * (size_t)h->nx * h->ny);
+  memcpy(out, h->st[h->cur], sizeof(double) * h->np * (size_t)h->nx * h->ny);
   return REF_OK;
 }
 
 int mclbm_ref_set_state(ref_t *h, const double *in) {
   if (!h || !in) return REF_EINVAL;
-  memcpy(h->st[h->cur], in, sizeof(double) * NPLANES * (size_t)h->nx * h->ny);
+  memcpy(h->st[h->cur], in, sizeof(double) * h->np * (size_t)h->nx * h->ny);
   if (!h->ready) {
     h->ready = 1;
     h->steps = 0;

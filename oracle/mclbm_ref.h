@@ -7,7 +7,8 @@
  * leg load this library. The CUDA library shares no code, header or constant with it.
  *
  * All arrays are row-major [plane][ny][nx], x fastest, j = 0 at the bottom wall, i = 0 at the
- * hot wall. Population planes are ordered f^w_0..8, f^p_0..8, g_0..8 and hold ABSOLUTE values.
+ * hot wall. Population planes are ordered f^w_0..8, f^p_0..8, g_0..8 (one thermal set) or
+ * f^w_0..8, f^p_0..8, g^w_0..8, g^p_0..8 (two thermal sets) and hold ABSOLUTE values.
  * Every function returns 0 on success or a negative REF_E* code.
  */
 #ifndef MCLBM_REF_H
@@ -43,6 +44,8 @@ extern "C" {
 #define REF_RHO_P 32u
 #define REF_UPX 64u
 #define REF_UPY 128u
+#define REF_THETA_W 256u /* theta of the base fluid's thermal set (= theta with one set) */
+#define REF_THETA_P 512u /* theta of the particles' thermal set (= theta with one set) */
 
 #define REF_INIT_REST 0
 #define REF_INIT_WARM 2     /* warm [4][ny][nx]: ux, uy, theta, phi; rho^w = 1 - phi */
@@ -56,6 +59,8 @@ typedef struct {
   uint32_t force_mask;                   /* REF_F_* */
   int periodic_x;                        /* test-only: periodic in x, no side walls */
   double body_fx;                        /* test-only: uniform x force density on f^w (lattice) */
+  int thermal_sets;                      /* 1: one set g of the mixture temperature; 2: g^w, g^p */
+  double tau_tp_override;                /* test-only: > 0 replaces the particles' thermal tau */
 } ref_props;
 
 /* Derived constants (create time, FP64). Ratios are suspension / base fluid. */

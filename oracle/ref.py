@@ -13,6 +13,7 @@ F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127
 UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
+THETA_W, THETA_P = 256, 512  # the thermal sets' own temperatures (= THETA with one set)
 INIT_REST, INIT_WARM, INIT_WARM_RHO = 0, 2, 3
 
 
@@ -20,7 +21,8 @@ class RefProps(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "rho_f", "cp_f", "k_f", "beta_f", "mu_f", "rho_p", "cp_p", "k_p", "beta_p",
         "T0", "dT", "g", "l_f", "Ma")] + [
-        ("force_mask", C.c_uint32), ("periodic_x", C.c_int), ("body_fx", C.c_double)]
+        ("force_mask", C.c_uint32), ("periodic_x", C.c_int), ("body_fx", C.c_double),
+        ("thermal_sets", C.c_int), ("tau_tp_override", C.c_double)]
 
 
 CONST_NAMES = (
@@ -145,6 +147,7 @@ class RefSolver:
         for k, v in overrides.items():
             setattr(p, k, v)
         self.props = p
+        self.np = 9 * (2 + p.thermal_sets)  # population planes
         h = C.c_void_p()
         _check(lib().mclbm_ref_create(self.nx, self.ny, Ra, Pr, phi, d_p, C.byref(p),
                                       C.byref(h)), "mclbm_ref_create")
@@ -209,13 +212,13 @@ class RefSolver:
         return r.value
 
     def get_state(self):
-        out = np.zeros((27, self.ny, self.nx))
+        out = np.zeros((self.np, self.ny, self.nx))
         _check(lib().mclbm_ref_get_state(self._h, _dp(out)), "mclbm_ref_get_state")
         return out
 
     def set_state(self, st):
         s = np.ascontiguousarray(st, dtype=np.float64)
-        assert s.shape == (27, self.ny, self.nx)
+        assert s.shape == (self.np, self.ny, self.nx)
         _check(lib().mclbm_ref_set_state(self._h, _dp(s)), "mclbm_ref_set_state")
         return self
 

@@ -681,3 +681,106 @@ def test_residual_from_field_snapshots(oracle_mod):
         den = np.sqrt((now[sel] ** 2).sum())
         terms.append(num / (K * den))
     assert r > 0 and abs(r - max(terms)) <= 1e-12 * r
+
+
+# ---------------------------------------------------------------- two thermal sets (Eq 19 x 2)
+def _two_set_uniform(nx, ny, rho_w, rho_p, th_w, th_p):
+    """Rest state, uniform partial densities and set temperatures (absolute populations)."""
+    node = np.concatenate([W * rho_w, W * rho_p, W * th_w, W * th_p])
+    return np.broadcast_to(node[:, None, None], (36, ny, nx)).copy()
+
+
+def test_two_sets_reduce_to_one_set(oracle_mod):
+    """With equal thermal relaxation times and equal initial sets, the two-set model (g^w, g^p
+    relaxing to the mixture temperature of Eq 33) stays with g^w = g^p and is the one-set model:
+    the same fields and Nusselt numbers (to rounding: the mixture weights and the local tau of
+    Eq 24 sum to one only to an ulp)."""
+    nx, ny, Ra, phi, d = 24, 20, 2e4, 0.03, 30e-9
+    tau = ref_solver(oracle_mod, nx, ny, Ra=Ra, phi=phi, d_p=d).consts()["tau_tw"]
+    one = ref_solver(oracle_mod, nx, ny, Ra=Ra, phi=phi, d_p=d, tau_tp_override=tau).init()
+    two = ref_solver(oracle_mod, nx, ny, Ra=Ra, phi=phi, d_p=d, tau_tp_override=tau,
+                     thermal_sets=2).init()
+    one.step(400)
+    two.step(400)
+    st = two.get_state()
+    assert st.shape[0] == 36
+    np.testing.assert_allclose(st[27:36], st[18:27], rtol=0, atol=1e-14)
+    which = (oracle_mod.UX | oracle_mod.UY | oracle_mod.THETA | oracle_mod.PHI | oracle_mod.RHO_W
+             | oracle_mod.UPX | oracle_mod.UPY)
+    a, b = one.fields(which), two.fields(which)
+    assert np.abs(a[0]).max() > 1e-4  # the flow is there
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(two.nusselt(), one.nusselt(), rtol=1e-12)
+
+
+def test_two_sets_conduction_limit(oracle_mod):
+    """No buoyancy, gravity or thermophoresis: both sets and the mixture settle on the exact
+    linear conduction profile, Nu = k_ns/k_f, whatever their relaxation times."""
+    mask = oracle_mod.F_DRAG | oracle_mod.F_BROWNIAN | oracle_mod.F_SAFFMAN | oracle_mod.F_MAGNUS
+    s = ref_solver(oracle_mod, 12, 9, Ra=1e3, phi=0.02, force_mask=mask, thermal_sets=2).init()
+    c = s.consts()
+    assert abs(c["tau_tw"] - c["tau_tp"]) > 1e-3  # distinct relaxation times
+    s.step(50)
+    nh, nc = s.nusselt()
+    assert abs(nh - c["k_ratio"]) < 1e-10 and abs(nc - c["k_ratio"]) < 1e-10
+    x = (np.arange(12) + 0.5) / 12
+    for f in s.fields(oracle_mod.THETA | oracle_mod.THETA_W | oracle_mod.THETA_P):
+        assert np.max(np.abs(f - (0.5 - x)[None, :])) < 1e-12
+
+
+def test_two_sets_equilibrate_at_mixture_temperature(oracle_mod):
+    """One step from rest with uniform but different set temperatures (periodic in x, no
+    forces): each set relaxes by 1/tau_theta^sigma towards the mixture temperature
+    (rho^w theta^w + r rho^p theta^p) / (rho^w + r rho^p), r = C_p,p / C_p,f (Eq 33 with the
+    components' heat capacities), tau_theta^w from the base fluid's diffusivity and tau_theta^p
+    from Eq 24 at the initial fractions (both derived independently)."""
+    nx, ny, Ra, Pr, phi, d = 6, 8, 1e4, 6.2, 0.04, 30e-9
+    s = ref_solver(oracle_mod, nx, ny, Ra=Ra, Pr=Pr, phi=phi, d_p=d, force_mask=0, periodic_x=1,
+                   thermal_sets=2)
+    c = s.consts()
+    ind = _independent_constants(nx, ny, Ra, Pr, phi, d)
+    rho_w, rho_p, th_w, th_p = c["rho_w0"], 1.3 * c["rho_p0"], 0.3, -0.2
+    s.init()
+    s.set_state(_two_set_uniform(nx, ny, rho_w, rho_p, th_w, th_p))
+    s.step(1)
+    th = s.fields(oracle_mod.THETA_W | oracle_mod.THETA_P)
+    r = 765.0 / 4179.0
+    th_ns = (rho_w * th_w + r * rho_p * th_p) / (rho_w + r * rho_p)
+    exp_w = th_w - (th_w - th_ns) / ind["tau_tw"]
+    exp_p = th_p - (th_p - th_ns) / ind["tau_tp"]
+    np.testing.assert_allclose(th[0], exp_w, rtol=1e-12)
+    np.testing.assert_allclose(th[1], exp_p, rtol=1e-12)
+    # the mixture temperature the fields report after the step is Eq 33 of the new set values
+    mix = s.fields(oracle_mod.THETA)[0]
+    np.testing.assert_allclose(mix, (rho_w * exp_w + r * rho_p * exp_p) / (rho_w + r * rho_p),
+                               rtol=1e-12)
+
+
+def test_two_sets_conserve_enthalpy_at_equal_tau(oracle_mod):
+    """Closed box (periodic in x, adiabatic top and bottom), fluid at rest, no forces, equal
+    relaxation times: streaming and the relaxation towards the Eq 33 mixture temperature
+    conserve the total enthalpy sum(rho^w theta^w + r rho^p theta^p) from nonuniform set
+    temperatures."""
+    nx, ny = 10, 12
+    tau = ref_solver(oracle_mod, nx, ny, Ra=1e4, phi=0.03, d_p=30e-9).consts()["tau_tw"]
+    s = ref_solver(oracle_mod, nx, ny, Ra=1e4, phi=0.03, d_p=30e-9, force_mask=0, periodic_x=1,
+                   thermal_sets=2, tau_tp_override=tau)
+    c = s.consts()
+    rng = np.random.default_rng(7)
+    st = _two_set_uniform(nx, ny, c["rho_w0"], c["rho_p0"], 0.0, 0.0)
+    thw = rng.uniform(-0.5, 0.5, (ny, nx))
+    thp = rng.uniform(-0.5, 0.5, (ny, nx))
+    st[18:27] = W[:, None, None] * thw[None]
+    st[27:36] = W[:, None, None] * thp[None]
+    s.init()
+    s.set_state(st)
+    r = 765.0 / 4179.0
+
+    def enthalpy():
+        f = s.fields(oracle_mod.RHO_W | oracle_mod.RHO_P | oracle_mod.THETA_W | oracle_mod.THETA_P)
+        return (f[0] * f[2] + r * f[1] * f[3]).sum()
+    h0 = enthalpy()
+    s.step(200)
+    f = s.fields(oracle_mod.THETA_W | oracle_mod.THETA_P)
+    assert np.abs(f[0] - f[1]).max() < 0.5 * np.abs(thw - thp).max()  # the sets exchanged heat
+    assert abs(enthalpy() - h0) <= 1e-12 * np.abs(thw).sum()
