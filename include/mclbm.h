@@ -55,12 +55,14 @@ extern "C" {
 /* ---- field selectors (mclbm_fields); outputs follow ascending bit order ------------------ */
 #define MCLBM_UX 1u    /* mixture (barycentric) velocity, Eq 32 */
 #define MCLBM_UY 2u
-#define MCLBM_THETA 4u /* temperature, theta in [-1/2, 1/2], Eq 31 */
+#define MCLBM_THETA 4u /* temperature, theta in [-1/2, 1/2], Eq 31 (Eq 33 with two sets) */
 #define MCLBM_PHI 8u   /* particle volume fraction rho^p rho_f / rho_p */
 #define MCLBM_RHO_W 16u /* base-fluid partial density (normalised by rho_f), Eq 29 */
 #define MCLBM_RHO_P 32u /* particle partial density (normalised by rho_f), Eq 29 */
 #define MCLBM_UPX 64u  /* particle-component velocity, Eq 30 */
 #define MCLBM_UPY 128u
+#define MCLBM_THETA_W 256u /* base fluid's thermal set (= MCLBM_THETA with one set), Eq 31 */
+#define MCLBM_THETA_P 512u /* particles' thermal set (= MCLBM_THETA with one set), Eq 31 */
 
 /* ---- initial states (mclbm_init) --------------------------------------------------------- */
 #define MCLBM_INIT_REST 0 /* rest, uniform phi, theta linear from +1/2 (hot) to -1/2 (cold) */
@@ -88,7 +90,20 @@ typedef struct mclbm_props {
   uint32_t force_mask;                   /* MCLBM_F_* bits */
   int32_t storage;                       /* MCLBM_STORE_F32, _F16 or _BF16 */
   int32_t rounding;                      /* MCLBM_ROUND_*: 16-bit stores only */
+  int32_t thermal_sets;                  /* 1: one thermal set g of the mixture temperature;
+                                            2: g^w and g^p (Eq 19 for both components), see
+                                            below */
 } mclbm_props;
+
+/* Two thermal sets (thermal_sets = 2; the paper's Eq 19 has one thermal population set per
+ * component): g^w and g^p stream with the same wall rules and relax, each with its own time
+ * (tau_theta^w, and tau_theta^p from Eq 24 at the initial fractions), towards the equilibrium at
+ * the mixture temperature of Eq 33, theta^ns = (rho^w theta^w + r rho^p theta^p) /
+ * (rho^w + r rho^p), r = C_p,p / C_p,f, as both f^sigma relax at the mixture velocity of Eq 32.
+ * theta^ns drives buoyancy, thermophoresis and Nu and is the THETA field; MCLBM_THETA_W and
+ * MCLBM_THETA_P select the sets' own temperatures. The state has 36 planes per time level
+ * (f^w, f^p, g^w, g^p: 288 bytes per lattice update in FP32); it steps with the plain tile
+ * kernel and cannot join a batch. With one set (the default) the state has 27 planes. */
 
 /* Derived create-time constants (FP64), for inspection and tests. Ratios are suspension over
  * base fluid (Eqs 7-11 at the initial phi); tau_* are the BGK relaxation times of Eqs 22-24;
@@ -155,7 +170,7 @@ int mclbm_stream_only(mclbm_t *h);
 
 /* Writes the selected moments of the post-stream populations (the macroscopic fields the
  * next step starts from) to dev_out, a device array [popcount(which)][ny][nx] FP32, planes
- * in ascending bit order of which (MCLBM_UX ... MCLBM_UPY). Async. */
+ * in ascending bit order of which (MCLBM_UX ... MCLBM_THETA_P). Async. */
 int mclbm_fields(mclbm_t *h, uint32_t which, float *dev_out);
 
 /* Mean Nusselt numbers of the hot (left) and cold (right) walls: k_ns/k_f times the mean
@@ -172,11 +187,12 @@ int mclbm_mass(mclbm_t *h, double *mass_w, double *mass_p);
  * FP64 sums. Replaces the snapshot. Syncs. MCLBM_EDIVERGED if non-finite. */
 int mclbm_residual(mclbm_t *h, double *r);
 
-/* Copies the 27 population planes [27][ny][nx] FP32 (f^w_0..8, f^p_0..8, g_0..8, directions
- * in the order of Eq 21: rest, +x, +y, -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)) between the
- * handle's current state and a caller device array. The planes hold deviations from the
- * initial conduction state: f^sigma_q - W_q rho_sigma0 (rho_w0, rho_p0 in mclbm_consts) and
- * g_q - W_q theta_c(i) with theta_c(i) = 1/2 - (i + 1/2)/nx.
+/* Copies the population planes [np][ny][nx] FP32 (np = 27: f^w_0..8, f^p_0..8, g_0..8; with
+ * two thermal sets np = 36: f^w, f^p, g^w, g^p; directions in the order of Eq 21: rest, +x, +y,
+ * -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)) between the handle's current state and a caller
+ * device array. The planes hold deviations from the initial conduction state:
+ * f^sigma_q - W_q rho_sigma0 (rho_w0, rho_p0 in mclbm_consts) and g_q - W_q theta_c(i) with
+ * theta_c(i) = 1/2 - (i + 1/2)/nx.
  * state_set also makes the state the post-collision state of step 0. Async. */
 int mclbm_state_get(mclbm_t *h, float *dev_out);
 int mclbm_state_set(mclbm_t *h, const float *dev_in);

@@ -16,6 +16,7 @@ F_BROWNIAN, F_THERMOPHORESIS, F_DRAG, F_SAFFMAN, F_MAGNUS, F_GRAVITY, F_BUOYANCY
     1, 2, 4, 8, 16, 32, 64)
 F_ALL = 127
 UX, UY, THETA, PHI, RHO_W, RHO_P, UPX, UPY = 1, 2, 4, 8, 16, 32, 64, 128
+THETA_W, THETA_P = 256, 512  # the thermal sets' own temperatures (= THETA with one set)
 INIT_REST, INIT_WARM, INIT_WARM_RHO = 0, 2, 3
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
@@ -48,7 +49,8 @@ class Props(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "rho_f", "cp_f", "k_f", "beta_f", "mu_f", "rho_p", "cp_p", "k_p", "beta_p",
         "T0_K", "dT_K", "g", "l_f", "Ma")] + [("force_mask", C.c_uint32),
-                                              ("storage", C.c_int32), ("rounding", C.c_int32)]
+                                              ("storage", C.c_int32), ("rounding", C.c_int32),
+                                              ("thermal_sets", C.c_int32)]
 
 
 CONST_NAMES = (
@@ -224,6 +226,7 @@ class Cavity:
         for k, v in prop_overrides.items():
             setattr(p, k, v)
         self.props = p
+        self.np = 9 * (2 + p.thermal_sets)  # population planes per time level
         self.device = torch.device(device if device is not None else "cuda")
         self._h = create(nx, ny, Ra, Pr, phi, d_p, p)
         nbytes = int(lib().mclbm_buffer_bytes(self._h))
@@ -319,7 +322,7 @@ class Cavity:
 
     def state_get(self, out=None):
         if out is None:
-            out = self.torch.empty((27, self.ny, self.nx), dtype=self.torch.float32,
+            out = self.torch.empty((self.np, self.ny, self.nx), dtype=self.torch.float32,
                                    device=self.device)
         self._check(lib().mclbm_state_get(self._h, C.c_void_p(out.data_ptr())),
                     "mclbm_state_get")
@@ -327,7 +330,7 @@ class Cavity:
 
     def state_set(self, st):
         assert st.dtype == self.torch.float32 and st.is_cuda and st.is_contiguous()
-        assert tuple(st.shape) == (27, self.ny, self.nx)
+        assert tuple(st.shape) == (self.np, self.ny, self.nx)
         self._check(lib().mclbm_state_set(self._h, C.c_void_p(st.data_ptr())), "mclbm_state_set")
         return self
 

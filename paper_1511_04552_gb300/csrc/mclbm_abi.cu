@@ -29,7 +29,7 @@ struct mclbm {
   int device = -1;
   char* state[2] = {nullptr, nullptr};  // two time levels, element type of L.storage
   float* snap = nullptr;     // [4][ny][nx]
-  float* staging = nullptr;  // [8][ny][nx]
+  float* staging = nullptr;  // [kFields][ny][nx]
   double* partials = nullptr;
   double* red = nullptr;
   int* err_dev = nullptr;       // device error word of the step kernels (bounded waits)
@@ -78,11 +78,11 @@ Regions regions(const mclbm_t* h) {
   const size_t n = (size_t)h->nx * h->ny;
   size_t off = 0;
   r.state = off;
-  off += align_up(2 * (size_t)kPlanes * h->L.plane * h->L.elem, 256);
+  off += align_up(2 * (size_t)h->L.np * h->L.plane * h->L.elem, 256);
   r.snap = off;
   off += align_up(4 * n * sizeof(float), 256);
   r.staging = off;
-  off += align_up(8 * n * sizeof(float), 256);
+  off += align_up(kFields * n * sizeof(float), 256);
   r.partials = off;
   off += align_up((size_t)kMaxRedBlocks * kRedWidth * sizeof(double), 256);
   r.red = off;
@@ -201,6 +201,7 @@ int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
     return MCLBM_EINVAL;
   if (p.rounding != MCLBM_ROUND_STOCHASTIC && p.rounding != MCLBM_ROUND_NEAREST)
     return MCLBM_EINVAL;
+  if (p.thermal_sets != 1 && p.thermal_sets != 2) return MCLBM_EINVAL;
   mclbm_t* h = new (std::nothrow) mclbm();
   if (!h) return MCLBM_EINVAL;
   h->nx = nx;
@@ -222,7 +223,8 @@ int mclbm_create(int nx, int ny, double Ra, double Pr, double phi, double d_p,
   h->L.elem = p.storage == MCLBM_STORE_F32 ? 4 : 2;
   h->L.pitch = (int)align_up((size_t)nx, 128 / h->L.elem);  // 128-byte rows
   h->L.plane = (size_t)h->L.pitch * ny;
-  h->cfg = choose_step_config(nx, ny);
+  h->L.np = p.thermal_sets == 2 ? kPlanes2 : kPlanes;
+  h->cfg = choose_step_config(nx, ny, h->L.np);
   *out = h;
   return MCLBM_OK;
 }
@@ -260,7 +262,7 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->buf_bytes = bytes;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->state[0] = h->buf + r.state;
-  h->state[1] = h->state[0] + (size_t)kPlanes * h->L.plane * h->L.elem;
+  h->state[1] = h->state[0] + (size_t)h->L.np * h->L.plane * h->L.elem;
   h->snap = reinterpret_cast<float*>(h->buf + r.snap);
   h->staging = reinterpret_cast<float*>(h->buf + r.staging);
   h->partials = reinterpret_cast<double*>(h->buf + r.partials);
@@ -269,7 +271,7 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->epoch = reinterpret_cast<uint32_t*>(h->buf + r.err + 4);
   // device-dependent set-up of the step kernel; the TMA variant falls back to the plain tile
   // kernel if the device cannot run it
-  h->cfg = choose_step_config(h->nx, h->ny);
+  h->cfg = choose_step_config(h->nx, h->ny, h->L.np);
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
   if (h->cfg.variant == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
@@ -339,7 +341,7 @@ int mclbm_stream_only(mclbm_t* h) {
 int mclbm_fields(mclbm_t* h, uint32_t which, float* dev_out) {
   int rc = ready(h, true);
   if (rc) return rc;
-  if (!dev_out || which == 0 || (which & ~0xFFu))
+  if (!dev_out || which == 0 || (which & ~kFieldMask))
     return fail(h, MCLBM_EINVAL, "bad field selection 0x%x or NULL output", which);
   CK(h, launch_fields(h->state[h->cur], h->L, h->k, which, dev_out, h->stream));
   return MCLBM_OK;
@@ -434,7 +436,7 @@ int mclbm_state_set(mclbm_t* h, const float* dev_in) {
 namespace {
 
 // Checkpoint file: this header, then the current time level's population planes exactly as
-// stored on the device (27 planes of pitch x ny elements of the storage type).
+// stored on the device (27 or 36 planes of pitch x ny elements of the storage type).
 struct CheckpointHeader {
   char magic[8];  // "MCLBMCK1"
   uint32_t version;
@@ -463,10 +465,11 @@ uint64_t props_hash(const mclbm_props& p) {
   fnv1a(x, &p.force_mask, sizeof(p.force_mask));
   fnv1a(x, &p.storage, sizeof(p.storage));
   fnv1a(x, &p.rounding, sizeof(p.rounding));
+  fnv1a(x, &p.thermal_sets, sizeof(p.thermal_sets));
   return x;
 }
 
-size_t level_bytes(const mclbm_t* h) { return (size_t)kPlanes * h->L.plane * h->L.elem; }
+size_t level_bytes(const mclbm_t* h) { return (size_t)h->L.np * h->L.plane * h->L.elem; }
 
 }  // namespace
 
@@ -546,7 +549,7 @@ int mclbm_run_host(mclbm_t* h, const float* warm_host, int64_t n, uint32_t which
                    float* fields_host, double* nu_hot, double* nu_cold) {
   int rc = ready(h, false);
   if (rc) return rc;
-  if ((which & ~0xFFu) || (which && !fields_host) || n < 0)
+  if ((which & ~kFieldMask) || (which && !fields_host) || n < 0)
     return fail(h, MCLBM_EINVAL, "bad arguments");
   const size_t nn = (size_t)h->nx * h->ny;
   if (warm_host) {
@@ -735,6 +738,7 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
     if (h->device != cavities[0]->device || h->L.storage != cavities[0]->L.storage)
       return MCLBM_EINVAL;
     if (h->nx > 65535 || h->ny > 16383) return MCLBM_EINVAL;
+    if (h->L.np != kPlanes) return MCLBM_EINVAL;  // one thermal set only
   }
   const BatchRegions r = batch_regions(n, cavities);
   if (bytes < r.total) return MCLBM_EINVAL;

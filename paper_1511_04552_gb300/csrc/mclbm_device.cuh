@@ -163,6 +163,36 @@ __device__ __forceinline__ void pull_node(const T* __restrict__ src, const Layou
   }
 }
 
+// Pull of the thermal set whose planes start at `base` (18: g or g^w; 27: g^p), with the wall
+// rules of pull_node.
+template <class T>
+__device__ __forceinline__ void pull_thermal(const T* __restrict__ src, const Layout& L, int i,
+                                             int j, int base, float* g, float s) {
+  using E = Elem<T>;
+  const size_t self = (size_t)j * L.pitch + i;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int si = i - ex(q), sj = j - ey(q);
+    const bool inx = (unsigned)si < (unsigned)L.nx;
+    const bool iny = (unsigned)sj < (unsigned)L.ny;
+    if (inx && iny)
+      g[q] = E::ldg(src + (size_t)(base + q) * L.plane + (size_t)sj * L.pitch + si);
+    else if (!inx)
+      g[q] = -E::ldg(src + (size_t)(base + opp(q)) * L.plane + self);
+    else
+      g[q] = E::ldg(src + (size_t)(base + mir(q)) * L.plane + (size_t)j * L.pitch + si);
+    if (ex(q) != 0) g[q] += (float)ex(q) * wq(q) * s;
+  }
+}
+
+// Eq 33 with two thermal sets: the mixture's deviation from theta_c, the heat-capacity
+// weighted mean of the sets' deviations (rho_w, rho_p the absolute partial densities).
+__device__ __forceinline__ float mixture_dev(const StepConsts& k, float rho_w, float rho_p,
+                                             float dev_w, float dev_p) {
+  const float cp = k.r_cp * rho_p;
+  return (rho_w * dev_w + cp * dev_p) / (rho_w + cp);
+}
+
 // theta_c(i): the linear conduction profile the g deviations are taken from
 __device__ __forceinline__ float theta_c(const StepConsts& k, int i) {
   return k.th_c0 - (float)i * k.inv_nx;

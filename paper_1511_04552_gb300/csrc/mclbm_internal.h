@@ -13,7 +13,10 @@
 namespace mcl {
 
 constexpr int kQ = 9;        // D2Q9 directions (Eq 21)
-constexpr int kPlanes = 27;  // f^w, f^p, g
+constexpr int kPlanes = 27;  // f^w, f^p, g (one thermal set)
+constexpr int kPlanes2 = 36; // f^w, f^p, g^w, g^p (two thermal sets)
+constexpr int kFields = 10;  // MCLBM_UX ... MCLBM_THETA_P
+constexpr uint32_t kFieldMask = (1u << kFields) - 1u;
 constexpr int kGraphSteps = 64;     // steps per captured graph (even: the buffers come back)
 constexpr int kMaxRedBlocks = 304;  // reduction partials: 2 CTAs per SM on 152 SMs
 constexpr int kRedWidth = 8;        // doubles per reduction partial
@@ -39,16 +42,19 @@ struct StepConsts {
   float th_c0;                // theta_c(0) = 1/2 - 1/(2 nx); theta_c(i) = th_c0 - i / nx
   uint32_t mask;              // MCLBM_F_* bits
   int has_p;                  // initial phi > 0
+  int two_sets;               // two thermal population sets (g^w, g^p)
+  float r_cp;                 // C_p,p / C_p,f: the heat-capacity weight of Eq 33
   double rho_w0_d, rho_p0_d;  // FP64 offsets and rho_f / rho_p for the initial fill
   double fr_d;
 };
 
-// Layout of the state inside the caller's buffer: 27 planes [ny][pitch] per time level.
+// Layout of the state inside the caller's buffer: np planes [ny][pitch] per time level.
 struct Layout {
   int nx, ny, pitch;  // pitch: elements per row, rows 128-byte aligned
   size_t plane;       // elements per plane = pitch * ny
   int storage;        // MCLBM_STORE_F32, _F16 or _BF16
   int elem;           // bytes per element (4 or 2)
+  int np;             // planes per time level: 27, or 36 with two thermal sets
 };
 
 struct StepArgs {
@@ -76,7 +82,7 @@ struct StepConfig {
   bool sr;      // 16-bit storage: stochastic rounding (else round to nearest)
   int vec;      // nodes per thread of the step kernels: 1 or 2 (0: chosen by lattice size)
 };
-StepConfig choose_step_config(int nx, int ny);
+StepConfig choose_step_config(int nx, int ny, int np);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
 // may fall back to variant 0. Needs the device current.
 cudaError_t prepare_step(StepConfig* c, const Layout& L);
@@ -117,7 +123,7 @@ cudaError_t launch_mass(const void* src, const Layout& L, double* partials, doub
 // the snapshot [4][ny][nx] (ux, uy, theta, phi) is replaced.
 cudaError_t launch_residual(const void* src, const Layout& L, const StepConsts& k, float* snap,
                             bool sums, double* partials, double* red, cudaStream_t st);
-// to_packed: stored level -> packed FP32 deviations [27][ny][nx]; else the reverse.
+// to_packed: stored level -> packed FP32 deviations [np][ny][nx]; else the reverse.
 cudaError_t launch_state_copy(const void* src, void* dst, const Layout& L, bool to_packed,
                               cudaStream_t st);
 

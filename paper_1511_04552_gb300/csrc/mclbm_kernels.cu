@@ -31,6 +31,11 @@ __global__ void stream_only_kernel(const T* __restrict__ src, T* __restrict__ ds
       dst[(size_t)(kQ + q) * L.plane + o] = Elem<T>::put(fp[q]);
       dst[(size_t)(2 * kQ + q) * L.plane + o] = Elem<T>::put(g[q]);
     }
+    if (L.np == kPlanes2) {  // g^p
+      pull_thermal<T>(src, L, i, j, 3 * kQ, g, s);
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) dst[(size_t)(3 * kQ + q) * L.plane + o] = Elem<T>::put(g[q]);
+    }
   }
 }
 
@@ -68,18 +73,24 @@ __global__ void init_kernel(T* __restrict__ dst, const Layout L, const StepConst
       dst[(size_t)q * L.plane + o] = Elem<T>::put((float)(W * (drw + rw * P)));
       dst[(size_t)(kQ + q) * L.plane + o] = Elem<T>::put((float)(W * (drp + rp * P)));
       dst[(size_t)(2 * kQ + q) * L.plane + o] = Elem<T>::put((float)(W * (dth + th * P)));
+      if (L.np == kPlanes2)
+        dst[(size_t)(3 * kQ + q) * L.plane + o] = Elem<T>::put((float)(W * (dth + th * P)));
     }
   }
 }
 
 // ---- macroscopic fields of the post-stream state ----------------------------------------------
-__device__ __forceinline__ void node_fields(const StepConsts& k, const Moments& m, int i,
-                                            float* v) {
+// thp: the particles' thermal set's deviation (= m.th with one set); v[kFields].
+__device__ __forceinline__ void node_fields(const StepConsts& k, const Moments& m, float thp,
+                                            int i, float* v) {
   const float rw = k.rho_w0 + m.rw, rp = k.rho_p0 + m.rp;
   const float rho = rw + rp;
+  const float tc = theta_c(k, i);
   v[0] = (m.mwx + m.mpx) / rho;
   v[1] = (m.mwy + m.mpy) / rho;
-  v[2] = theta_c(k, i) + m.th;
+  v[2] = tc + (k.two_sets ? mixture_dev(k, rw, rp, m.th, thp) : m.th);
+  v[8] = tc + m.th;
+  v[9] = tc + thp;
   v[3] = rp * k.phi_per_rho_p;
   v[4] = rw;
   v[5] = rp;
@@ -97,11 +108,17 @@ __global__ void fields_kernel(const T* __restrict__ src, const Layout L, const S
     const int i = (int)(t % L.nx), j = (int)(t / L.nx);
     float fw[kQ], fp[kQ], g[kQ];
     pull_node<T, true>(src, L, i, j, fw, fp, g, k.inv_nx);
-    float v[8];
-    node_fields(k, moments_of(fw, fp, g), i, v);
+    const Moments m = moments_of(fw, fp, g);
+    float thp = m.th;
+    if (k.two_sets) {
+      pull_thermal<T>(src, L, i, j, 3 * kQ, g, k.inv_nx);
+      thp = sum9(g);
+    }
+    float v[kFields];
+    node_fields(k, m, thp, i, v);
     int slot = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
+    for (int b = 0; b < kFields; ++b)
       if (which & (1u << b)) out[(int64_t)(slot++) * n + t] = v[b];
   }
 }
@@ -148,19 +165,27 @@ __global__ void final_reduce_kernel(const double* __restrict__ partials, int cou
 // (8 T_h - 9 theta_0 + theta_1)/3 = 1/nx + (theta'_1 - 9 theta'_0)/3 and the cold-wall twin
 // (9 theta_{n-1} - theta_{n-2} - 8 T_c)/3 = 1/nx + (9 theta'_{n-1} - theta'_{n-2})/3.
 template <class T>
-__global__ void nusselt_kernel(const T* __restrict__ src, const Layout L, float s,
+__global__ void nusselt_kernel(const T* __restrict__ src, const Layout L, const StepConsts k,
                                double* __restrict__ red) {
+  const float s = k.inv_nx;
+  // the (mixture) temperature's deviation from theta_c at node (i, j) after streaming
+  auto dev = [&](int i, int j) -> float {
+    float fw[kQ], fp[kQ], g[kQ];
+    if (!k.two_sets) {
+      pull_node<T, false>(src, L, i, j, fw, fp, g, s);
+      return sum9(g);
+    }
+    pull_node<T, true>(src, L, i, j, fw, fp, g, s);
+    const float dw = sum9(g);
+    pull_thermal<T>(src, L, i, j, 3 * kQ, g, s);
+    return mixture_dev(k, k.rho_w0 + sum9(fw), k.rho_p0 + sum9(fp), dw, sum9(g));
+  };
   double acc[2] = {0.0, 0.0};
   for (int j = threadIdx.x; j < L.ny; j += blockDim.x) {
-    float fw[kQ], fp[kQ], g[kQ];
-    pull_node<T, false>(src, L, 0, j, fw, fp, g, s);
-    const double t0 = sum9(g);
-    pull_node<T, false>(src, L, 1, j, fw, fp, g, s);
-    const double t1 = sum9(g);
-    pull_node<T, false>(src, L, L.nx - 1, j, fw, fp, g, s);
-    const double c0 = sum9(g);
-    pull_node<T, false>(src, L, L.nx - 2, j, fw, fp, g, s);
-    const double c1 = sum9(g);
+    const double t0 = dev(0, j);
+    const double t1 = dev(1, j);
+    const double c0 = dev(L.nx - 1, j);
+    const double c1 = dev(L.nx - 2, j);
     const double slope = 1.0 / (double)L.nx;
     acc[0] += slope + (t1 - 9.0 * t0) / 3.0;
     acc[1] += slope + (9.0 * c0 - c1) / 3.0;
@@ -201,8 +226,14 @@ __global__ void residual_kernel(const T* __restrict__ src, const Layout L, const
     const int i = (int)(t % L.nx), j = (int)(t / L.nx);
     float fw[kQ], fp[kQ], g[kQ];
     pull_node<T, true>(src, L, i, j, fw, fp, g, k.inv_nx);
-    float v[8];
-    node_fields(k, moments_of(fw, fp, g), i, v);
+    const Moments m = moments_of(fw, fp, g);
+    float thp = m.th;
+    if (k.two_sets) {
+      pull_thermal<T>(src, L, i, j, 3 * kQ, g, k.inv_nx);
+      thp = sum9(g);
+    }
+    float v[kFields];
+    node_fields(k, m, thp, i, v);
     if (sums) {
       const double now[4] = {v[0], v[1], v[2], v[3]};
       double d[4];
@@ -225,7 +256,7 @@ template <class T>
 __global__ void state_copy_kernel(const void* __restrict__ src_v, void* __restrict__ dst_v,
                                   const Layout L, int to_packed) {
   const int64_t n = (int64_t)L.nx * L.ny;
-  const int64_t total = n * kPlanes;
+  const int64_t total = n * L.np;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = t / n, r = t % n;
@@ -267,7 +298,7 @@ cudaError_t by_storage(int storage, F&& f) {
   }
 }
 
-StepConfig choose_step_config(int nx, int ny) {
+StepConfig choose_step_config(int nx, int ny, int np) {
   StepConfig c;
   // default: TMA-staged tiles for lattices with a few tiles per SM, the plain tile kernel below.
   // MCLBM_STEP_VARIANT = tile | tma overrides (diagnostics and comparisons).
@@ -280,6 +311,10 @@ StepConfig choose_step_config(int nx, int ny) {
   // MCLBM_STEP_VEC = 1 | 2 forces the nodes per thread (comparisons; default by lattice size)
   const char* vv = std::getenv("MCLBM_STEP_VEC");
   c.vec = (vv && (vv[0] == '1' || vv[0] == '2') && vv[1] == 0) ? vv[0] - '0' : 0;
+  if (np != kPlanes) {  // two thermal sets: the plain tile kernel, one node per thread
+    c.variant = 0;
+    c.vec = 1;
+  }
   return c;
 }
 
@@ -398,7 +433,7 @@ cudaError_t launch_nusselt(const void* src, const Layout& L, const StepConsts& k
                            cudaStream_t st) {
   return by_storage(L.storage, [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    nusselt_kernel<T><<<1, 256, 0, st>>>(static_cast<const T*>(src), L, k.inv_nx, red);
+    nusselt_kernel<T><<<1, 256, 0, st>>>(static_cast<const T*>(src), L, k, red);
     return cudaGetLastError();
   });
 }
@@ -430,7 +465,7 @@ cudaError_t launch_residual(const void* src, const Layout& L, const StepConsts& 
 
 cudaError_t launch_state_copy(const void* src, void* dst, const Layout& L, bool to_packed,
                               cudaStream_t st) {
-  const int64_t n = (int64_t)L.nx * L.ny * kPlanes;
+  const int64_t n = (int64_t)L.nx * L.ny * L.np;
   return by_storage(L.storage, [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
     state_copy_kernel<T><<<grid_for(n, 256, 8192), 256, 0, st>>>(src, dst, L, to_packed ? 1 : 0);

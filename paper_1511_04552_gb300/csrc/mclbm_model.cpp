@@ -38,6 +38,7 @@ void props_default(mclbm_props* p) {
   p->force_mask = MCLBM_F_ALL;
   p->storage = MCLBM_STORE_F32;
   p->rounding = MCLBM_ROUND_STOCHASTIC;
+  p->thermal_sets = 1;
 }
 
 int derive_consts(int nx, int ny, double Ra, double Pr, double phi, double d_p,
@@ -165,6 +166,8 @@ StepConsts fold_step_consts(int nx, int ny, double phi, double d_p, const mclbm_
   k.th_c0 = (float)(0.5 - 0.5 / nx);
   k.mask = p.force_mask;
   k.has_p = phi > 0.0 ? 1 : 0;
+  k.two_sets = p.thermal_sets == 2 ? 1 : 0;
+  k.r_cp = (float)(p.cp_p / p.cp_f);
   k.rho_w0_d = c.rho_w0;
   k.rho_p0_d = c.rho_p0;
   k.fr_d = fr;

@@ -236,6 +236,23 @@ __device__ __forceinline__ void pull1(const Acc& acc, const Layout& L, int i, in
   }
 }
 
+// The thermal set whose planes start at `base` (27: g^p of the two-thermal-set state) of one
+// node, with the thermal wall rules.
+template <class Acc>
+__device__ __forceinline__ void pull1_thermal(const Acc& acc, const Layout& L, int i, int j, int d,
+                                              int base, float* g) {
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int si = i - ex(q), sj = j - ey(q);
+    const bool inx = (unsigned)si < (unsigned)L.nx;
+    const bool iny = (unsigned)sj < (unsigned)L.ny;
+    if (inx && iny)
+      g[q] = acc.a1(base + q, d - ex(q), -ey(q));
+    else
+      g[q] = inx ? acc.a1(base + mir(q), d - ex(q), 0) : -acc.a1(base + opp(q), d, 0);
+  }
+}
+
 // V nodes (i, i + V - 1). For V = 2, lane y of a pair whose second node lies outside the cavity
 // (i + 1 == nx) repeats lane x.
 template <int V, bool FULL, class Acc>
@@ -332,6 +349,18 @@ __device__ __forceinline__ X mom_y(const X* a) {
   return add(add(sub(a[2], a[4]), sub(a[5], a[8])), sub(a[6], a[7]));
 }
 
+// Eq 33 with two thermal sets: the mixture temperature's deviation from theta_c, in the stored
+// units of T, from the sums of the populations of the four sets (srw, srp: f^w, f^p; sw, sp:
+// g^w, g^p): the heat-capacity weighted mean (weights rho^w and r rho^p, r = C_p,p / C_p,f).
+template <class T>
+__device__ __forceinline__ float mixture_s(const StepConsts& k, float srw, float srp, float sw,
+                                           float sp) {
+  constexpr float iS = 1.0f / (float)(1 << St<T>::kLog2S);
+  const float rw = fma(srw, iS, k.rho_w0), rp = fma(srp, iS, k.rho_p0);
+  const float cp = mul(k.r_cp, rp);
+  return mul(fma(rw, sw, mul(cp, sp)), rcp(add(rw, cp)));
+}
+
 // Nearest wall of node (i, j) (ties: left, right, bottom, top): zeta = (2z/H)(0.63 - 2z/H) times
 // the inward normal (Table 1 Magnus profile).
 __device__ __forceinline__ void magnus_profile(const StepConsts& k, const Layout& L, int i, int j,
@@ -351,21 +380,28 @@ __device__ __forceinline__ void magnus_profile(const StepConsts& k, const Layout
 // Steps A2-A7 for the V nodes (i, ..., i + V - 1) of row j. Populations, their moments and the
 // neighbours' theta and rho^p deviations thE..rpS (ghosts applied by the caller; theta_c's
 // slope -1/nx is added to d theta/dx here) are in the stored units of T (S times the
-// deviations); out(p, v) receives the 27 post-collision values in the same units.
-template <int V, bool ALLF, class T, class Sink>
+// deviations); out(p, v) receives the 27 post-collision values in the same units. TWO: the
+// two-thermal-set state (g = g^w, gp = g^p; theta is the Eq 33 mixture; 36 outputs).
+template <int V, bool ALLF, class T, bool TWO, class Sink>
 __device__ __forceinline__ void collide(const StepConsts& k, const Layout& L, Sink& out, int i,
                                         int j, const vec<V>* fw, const vec<V>* fp,
-                                        const vec<V>* g, vec<V> thE, vec<V> thW, vec<V> thN,
-                                        vec<V> thS, vec<V> rpE, vec<V> rpW, vec<V> rpN,
-                                        vec<V> rpS) {
+                                        const vec<V>* g, const vec<V>* gp, vec<V> thE,
+                                        vec<V> thW, vec<V> thN, vec<V> thS, vec<V> rpE,
+                                        vec<V> rpW, vec<V> rpN, vec<V> rpS) {
   using X = vec<V>;
+  static_assert(!TWO || V == 1, "two thermal sets: one node per thread");
   constexpr float S = (float)(1 << St<T>::kLog2S), iS = 1.0f / S;
   // x / S (exact; no instruction when S = 1)
   auto unscale = [&](X x) {
     if constexpr (St<T>::kLog2S == 0) return x; else return mul(x, bc<V>(iS));
   };
   const uint32_t mask = ALLF ? MCLBM_F_ALL : k.mask;
-  const X mrw = sum9(fw), mrp = sum9(fp), mth = sum9(g);
+  const X mrw = sum9(fw), mrp = sum9(fp);
+  X mth;
+  if constexpr (TWO)
+    mth = mixture_s<T>(k, mrw, mrp, sum9(g), sum9(gp));
+  else
+    mth = sum9(g);
   const X mwx = mom_x(fw), mwy = mom_y(fw), mpx = mom_x(fp), mpy = mom_y(fp);
   // theta_c of each node from its own column (so a lane rounds like the node alone)
   const X thc = mk<V>(fma(-(float)i, k.inv_nx, k.th_c0), fma(-(float)(i + 1), k.inv_nx, k.th_c0));
@@ -493,14 +529,20 @@ __device__ __forceinline__ void collide(const StepConsts& k, const Layout& L, Si
   // plus the drop of theta_c along the link that streaming left out, (1 - 1/tau) W_q e_qx / nx.
   // Opposite directions share the even part of P_q (B (e.u)^2 - C u.u) and negate the odd part
   // (A e.u), the forcing and the theta_c drop, so the loop runs over the four pairs (q, -q).
-  const X tau_t = fma(Yw, bc<V>(k.tau_tw), mul(Yp, bc<V>(k.tau_tp)));  // Eq 24, local fractions
-  const X om_t = rcp(tau_t);
+  // thermal relaxation: one set with tau of Eq 24 at the local fractions, or two sets with
+  // their own times (g^w as om_t, g^p as om_t2)
+  const X om_t = TWO ? bc<V>(rcp(k.tau_tw))
+                     : rcp(fma(Yw, bc<V>(k.tau_tw), mul(Yp, bc<V>(k.tau_tp))));
+  const X om_t2 = bc<V>(TWO ? rcp(k.tau_tp) : 0.0f);
+  const X keep_t2 = sub(bc<V>(1.0f), om_t2);
   const X om_w = bc<V>(k.inv_tau_w), om_p = bc<V>(k.inv_tau_p);
   const X keep_w = bc<V>(sub(1.0f, k.inv_tau_w)), keep_p = bc<V>(sub(1.0f, k.inv_tau_p));
   const X keep_t = sub(bc<V>(1.0f), om_t);
   const X usq = fma(ux, ux, mul(uy, uy));
   const X ck1 = mul(keep_t, bc<V>(mul(S * wq(1), k.inv_nx)));
   const X ck5 = mul(keep_t, bc<V>(mul(S * wq(5), k.inv_nx)));
+  const X ck1b = mul(keep_t2, bc<V>(mul(S * wq(1), k.inv_nx)));
+  const X ck5b = mul(keep_t2, bc<V>(mul(S * wq(5), k.inv_nx)));
   X sw = bc<V>(0.0f), sp = bc<V>(0.0f), sg = bc<V>(0.0f);  // half the sum of the moving equilibria
 #pragma unroll
   for (int pr = 0; pr < 4; ++pr) {
@@ -528,11 +570,17 @@ __device__ __forceinline__ void collide(const StepConsts& k, const Layout& L, Si
     out(kQ + qo, fma(fp[qo], keep_p, fma(om_p, sub(tp, dp), neg(Sp))));
     out(2 * kQ + q, fma(g[q], keep_t, fma(om_t, add(tg, dg), ck)));
     out(2 * kQ + qo, fma(g[qo], keep_t, fma(om_t, sub(tg, dg), neg(ck))));
+    if constexpr (TWO) {  // g^p towards the same (mixture) equilibrium
+      const X ckb = q == 1 ? ck1b : (q == 5 ? ck5b : (q == 6 ? neg(ck5b) : bc<V>(0.0f)));
+      out(3 * kQ + q, fma(gp[q], keep_t2, fma(om_t2, add(tg, dg), ckb)));
+      out(3 * kQ + qo, fma(gp[qo], keep_t2, fma(om_t2, sub(tg, dg), neg(ckb))));
+    }
   }
   // rest populations: equilibrium = zeroth moment minus the moving equilibria
   out(0, fma(fw[0], keep_w, mul(om_w, fma(bc<V>(-2.0f), sw, mrw))));
   out(kQ, fma(fp[0], keep_p, mul(om_p, fma(bc<V>(-2.0f), sp, mrp))));
   out(2 * kQ, fma(g[0], keep_t, mul(om_t, fma(bc<V>(-2.0f), sg, mth))));
+  if constexpr (TWO) out(3 * kQ, fma(gp[0], keep_t2, mul(om_t2, fma(bc<V>(-2.0f), sg, mth))));
 }
 
 // ---- output sinks ------------------------------------------------------------------------------
@@ -603,56 +651,77 @@ __device__ __forceinline__ void put_mom<float2>(float* row, int col, float2 v) {
   *reinterpret_cast<float2*>(row + col) = v;
 }
 
-// Phase 1 of a tile: pulls of the thread's nodes (kept in fw, fp, g) and of its ring task;
-// their theta' and rho'^p go to the moment tile. acc_at(dx, dy) returns the accessor of the
-// node at tile position (dx, dy).
-template <int TX, int TY, int V, class AccAt>
-__device__ __forceinline__ void tile_pull(const AccAt& acc_at, const Layout& L, int i0, int j0,
-                                          int t, MomTile<TX, TY>& mt, vec<V>* fw, vec<V>* fp,
-                                          vec<V>* g) {
+// Phase 1 of a tile: pulls of the thread's nodes (kept in fw, fp, g and, with two thermal
+// sets, gp) and of its ring task; their theta' (the Eq 33 mixture with two sets) and rho'^p go
+// to the moment tile. acc_at(dx, dy) returns the accessor of the node at tile position (dx, dy).
+template <int TX, int TY, int V, class T, bool TWO, class AccAt>
+__device__ __forceinline__ void tile_pull(const AccAt& acc_at, const Layout& L,
+                                          const StepConsts& k, int i0, int j0, int t,
+                                          MomTile<TX, TY>& mt, vec<V>* fw, vec<V>* fp, vec<V>* g,
+                                          vec<V>* gp) {
+  static_assert(!TWO || V == 1, "two thermal sets: one node per thread");
   const TileThread<TX, TY, V> tt(t);
   const int i = i0 + V * tt.c, j = j0 + tt.ty;
   if (i < L.nx && j < L.ny) {
     pull<V, true>(acc_at(V * tt.c, tt.ty), L, i, j, fw, fp, g);
-    put_mom(mt.th[tt.ty + 1], V * tt.c + 2, sum9(g));
+    if constexpr (TWO) {
+      pull1_thermal(acc_at(tt.c, tt.ty), L, i, j, 0, 3 * kQ, gp);
+      put_mom(mt.th[tt.ty + 1], tt.c + 2, mixture_s<T>(k, sum9(fw), sum9(fp), sum9(g), sum9(gp)));
+    } else {
+      put_mom(mt.th[tt.ty + 1], V * tt.c + 2, sum9(g));
+    }
     put_mom(mt.rp[tt.ty + 1], V * tt.c + 2, sum9(fp));
   }
+  // a ring node's moments: theta' (or the mixture's) and rho'^p of the pulled node
+  auto ring1 = [&](int dx, int dy, int hi, int hj, float& th, float& rp) {
+    float hw[kQ], hp[kQ], hg[kQ];
+    if constexpr (TWO) {
+      float hg2[kQ];
+      pull1<true>(acc_at(dx, dy), L, hi, hj, 0, hw, hp, hg);
+      pull1_thermal(acc_at(dx, dy), L, hi, hj, 0, 3 * kQ, hg2);
+      th = mixture_s<T>(k, sum9(hw), sum9(hp), sum9(hg), sum9(hg2));
+    } else {
+      pull1<false>(acc_at(dx, dy), L, hi, hj, 0, nullptr, hp, hg);
+      th = sum9(hg);
+    }
+    rp = sum9(hp);
+  };
   constexpr int NR = V == 2 ? TX : 2 * TX;  // ring-row tasks
   if (t < NR) {  // ring rows: below and above the tile
     const int hy = t < NR / 2 ? -1 : TY;
     const int hx = V * (t % (NR / 2));
     const int hi = i0 + hx, hj = j0 + hy;
     if (hj >= 0 && hj < L.ny && hi < L.nx) {
-      vec<V> hp[kQ], hg[kQ];
-      pull<V, false>(acc_at(hx, hy), L, hi, hj, nullptr, hp, hg);
-      put_mom(mt.th[hy + 1], hx + 2, sum9(hg));
-      put_mom(mt.rp[hy + 1], hx + 2, sum9(hp));
+      if constexpr (V == 1) {
+        float th, rp;
+        ring1(hx, hy, hi, hj, th, rp);
+        mt.th[hy + 1][hx + 2] = th;
+        mt.rp[hy + 1][hx + 2] = rp;
+      } else {
+        vec<V> hp[kQ], hg[kQ];
+        pull<V, false>(acc_at(hx, hy), L, hi, hj, nullptr, hp, hg);
+        put_mom(mt.th[hy + 1], hx + 2, sum9(hg));
+        put_mom(mt.rp[hy + 1], hx + 2, sum9(hp));
+      }
     }
   } else if (t < NR + (V == 2 ? TY : 2 * TY)) {  // ring columns
     const int r = t - NR;
     const int hy = V == 2 ? r : r % TY, hj = j0 + hy;
-    float hp[kQ], hg[kQ];
     // V = 2: both sides in one thread; V = 1: left for r < TY, right otherwise
     const bool left = V == 2 || r < TY, right = V == 2 || r >= TY;
-    if (hj < L.ny && left && i0 > 0) {
-      pull1<false>(acc_at(-1, hy), L, i0 - 1, hj, 0, nullptr, hp, hg);
-      mt.th[hy + 1][1] = sum9(hg);
-      mt.rp[hy + 1][1] = sum9(hp);
-    }
-    if (hj < L.ny && right && i0 + TX < L.nx) {
-      pull1<false>(acc_at(TX, hy), L, i0 + TX, hj, 0, nullptr, hp, hg);
-      mt.th[hy + 1][TX + 2] = sum9(hg);
-      mt.rp[hy + 1][TX + 2] = sum9(hp);
-    }
+    if (hj < L.ny && left && i0 > 0) ring1(-1, hy, i0 - 1, hj, mt.th[hy + 1][1], mt.rp[hy + 1][1]);
+    if (hj < L.ny && right && i0 + TX < L.nx)
+      ring1(TX, hy, i0 + TX, hj, mt.th[hy + 1][TX + 2], mt.rp[hy + 1][TX + 2]);
   }
 }
 
 // Phase 2 of a tile (after a barrier): neighbours' moments with the wall ghosts, then the
 // collision of the thread's nodes into the sink.
-template <bool ALLF, int TX, int TY, int V, class T, class Sink>
+template <bool ALLF, int TX, int TY, int V, class T, bool TWO, class Sink>
 __device__ __forceinline__ void tile_collide(const StepConsts& k, const Layout& L, int i0, int j0,
                                              int t, const MomTile<TX, TY>& mt, const vec<V>* fw,
-                                             const vec<V>* fp, const vec<V>* g, Sink& out) {
+                                             const vec<V>* fp, const vec<V>* g, const vec<V>* gp,
+                                             Sink& out) {
   using X = vec<V>;
   const TileThread<TX, TY, V> tt(t);
   const int i = i0 + V * tt.c, j = j0 + tt.ty;
@@ -683,7 +752,8 @@ __device__ __forceinline__ void tile_collide(const StepConsts& k, const Layout& 
   const float rpE0 = i + 1 < L.nx ? (V == 2 ? rp1 : mt.rp[r][c + 1]) : rp0;
   const float thE1 = V == 2 && i + 2 < L.nx ? mt.th[r][c + 2] : -th1;
   const float rpE1 = V == 2 && i + 2 < L.nx ? mt.rp[r][c + 2] : rp1;
-  collide<V, ALLF, T>(k, L, out, i, j, fw, fp, g, mk<V>(thE0, thE1), mk<V>(thW0, th0), thN, thS,
+  collide<V, ALLF, T, TWO>(k, L, out, i, j, fw, fp, g, gp, mk<V>(thE0, thE1), mk<V>(thW0, th0),
+                           thN, thS,
                    mk<V>(rpE0, rpE1), mk<V>(rpW0, rp0), rpN, rpS);
 }
 
@@ -704,7 +774,7 @@ struct MinBlocks {
 };
 
 // Plain tile kernel (small lattices): pulls from global memory (L1/L2), one tile per CTA.
-template <class T, bool SR, bool ALLF, int V>
+template <class T, bool SR, bool ALLF, int V, bool TWO = false>
 __global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW>::value)
     step_pair_tile_kernel(const StepArgs a) {
   constexpr int kTX = kTileW;
@@ -713,20 +783,20 @@ __global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW
   const T* __restrict__ src = static_cast<const T*>(a.src);
   const int t = threadIdx.x;
   const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
-  vec<V> fw[kQ], fp[kQ], g[kQ];
+  vec<V> fw[kQ], fp[kQ], g[kQ], gp[TWO ? kQ : 1];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step has completed
   auto acc_at = [&](int dx, int dy) {
     return GlobAcc<T>{src + (ptrdiff_t)(j0 + dy) * L.pitch + (i0 + dx), L.pitch, L.plane};
   };
-  tile_pull<kTX, kTY, V>(acc_at, L, i0, j0, t, mt, fw, fp, g);
+  tile_pull<kTX, kTY, V, T, TWO>(acc_at, L, a.k, i0, j0, t, mt, fw, fp, g, gp);
   __syncthreads();
   const TileThread<kTX, kTY, V> tt(t);
   const int i = i0 + V * tt.c, j = j0 + tt.ty;
   const size_t o = (size_t)j * L.pitch + i;
   GlobSink<T, SR, V> out{static_cast<T*>(a.dst) + o, L.plane,
                          SR ? mix32((uint32_t)o ^ step_hash(a)) : 0u, i + 1 < L.nx};
-  tile_collide<ALLF, kTX, kTY, V, T>(a.k, L, i0, j0, t, mt, fw, fp, g, out);
+  tile_collide<ALLF, kTX, kTY, V, T, TWO>(a.k, L, i0, j0, t, mt, fw, fp, g, gp, out);
 }
 
 // Shared memory of the TMA-staged kernels: one input window and, where it fits the CTAs per
@@ -799,7 +869,7 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
     vec<V> fw[kQ], fp[kQ], g[kQ];
     if (ok) {
       auto acc_at = [&](int dx, int dy) { return WinAcc<T, kTX>{w + (2 + dy) * WX + (XO + dx)}; };
-      tile_pull<kTX, kTY, V>(acc_at, L, d.i0, d.j0, t, mt, fw, fp, g);
+      tile_pull<kTX, kTY, V, T, false>(acc_at, L, d.k, d.i0, d.j0, t, mt, fw, fp, g, nullptr);
     } else {
       s_abort = 1;
     }
@@ -825,11 +895,13 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
     const uint32_t seed = SR ? mix32((uint32_t)o ^ d.hash) : 0u;
     if constexpr (STORE_TMA) {
       TileSink<T, SR, kTX * kTY, V> out{ob + tt.ty * kTX + V * tt.c, seed};
-      tile_collide<ALLF, kTX, kTY, V, T>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, out);
+      tile_collide<ALLF, kTX, kTY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
+                                                out);
       tma::fence_proxy_async();  // generic-proxy writes of the output tile before the TMA store
     } else {
       GlobSink<T, SR, V> out{static_cast<T*>(d.dst) + o, L.plane, seed, i + 1 < L.nx};
-      tile_collide<ALLF, kTX, kTY, V, T>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, out);
+      tile_collide<ALLF, kTX, kTY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
+                                                out);
     }
     __syncthreads();  // the moment tile and the output tile are free again
     if (STORE_TMA && t == 0) {
@@ -910,6 +982,14 @@ cudaError_t prepare_pair_tma_t(StepConfig* c, const Layout& L) {
 template <class T, bool SR, bool ALLF, int V>
 cudaError_t launch_pair_t4(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,
                            cudaLaunchConfig_t& cfg) {
+  constexpr int kTX = kTileW;
+  if (a.k.two_sets) {  // two thermal sets: the plain tile kernel, one node per thread
+    if (c.variant == 2 || V != 1 || ALLF) return cudaErrorInvalidValue;
+    cfg.gridDim = dim3((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
+    cfg.blockDim = dim3(Threads<1, kTileW>::value);
+    cfg.dynamicSmemBytes = 0;
+    return cudaLaunchKernelEx(&cfg, step_pair_tile_kernel<T, SR, false, 1, true>, a);
+  }
   if (c.variant == 2) {
     if (!map || c.grid < 1) return cudaErrorInvalidValue;
     cfg.gridDim = dim3(c.grid);
@@ -917,7 +997,6 @@ cudaError_t launch_pair_t4(const StepArgs& a, const StepConfig& c, const CUtenso
     cfg.dynamicSmemBytes = TmaPair<T, V, kTileW>::SMEM;
     return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<T, SR, ALLF, V>, map[0], map[1], a);
   }
-  constexpr int kTX = kTileW;
   cfg.gridDim = dim3((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
   cfg.blockDim = dim3(Threads<V, kTileW>::value);
   cfg.dynamicSmemBytes = 0;
@@ -943,7 +1022,7 @@ cudaError_t launch_pair_t(const StepArgs& a, const StepConfig& c, const CUtensor
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const bool all = a.k.mask == MCLBM_F_ALL;
+  const bool all = a.k.mask == MCLBM_F_ALL && !a.k.two_sets;
   const bool sr = c.sr && sizeof(T) == 2;
   if (sr)
     return all ? launch_pair_t3<T, true, true>(a, c, map, cfg)

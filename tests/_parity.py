@@ -61,26 +61,28 @@ def compare_fields(gpu, ref, rtol=FIELD_RTOL):
     return errs, bad
 
 
-def _offsets(consts, nx, ny):
-    """Per-plane offsets of the stored deviations: W_q rho_sigma0 for f, W_q theta_c(i) for g."""
-    off = np.zeros((27, ny, nx))
+def _offsets(consts, np_, nx, ny):
+    """Per-plane offsets of the stored deviations: W_q rho_sigma0 for f, W_q theta_c(i) for each
+    thermal set (np_ = 27 or 36 planes)."""
+    off = np.zeros((np_, ny, nx))
     off[:9] = (W * consts["rho_w0"])[:, None, None]
     off[9:18] = (W * consts["rho_p0"])[:, None, None]
     th_c = 0.5 - (np.arange(nx) + 0.5) / nx
-    off[18:] = W[:, None, None] * th_c[None, None, :]
+    for b in range(18, np_, 9):
+        off[b:b + 9] = W[:, None, None] * th_c[None, None, :]
     return off
 
 
 def dev_to_abs(dev, consts):
     dev = np.asarray(dev, dtype=np.float64)
-    return dev + _offsets(consts, dev.shape[2], dev.shape[1])
+    return dev + _offsets(consts, dev.shape[0], dev.shape[2], dev.shape[1])
 
 
 def abs_to_dev(st_abs, consts):
     st_abs = np.asarray(st_abs, dtype=np.float64)
-    return st_abs - _offsets(consts, st_abs.shape[2], st_abs.shape[1])
+    return st_abs - _offsets(consts, st_abs.shape[0], st_abs.shape[2], st_abs.shape[1])
 
 
 def gpu_state_abs(gpu):
-    """The GPU state as absolute FP64 populations [27][ny][nx]."""
+    """The GPU state as absolute FP64 populations [27 or 36][ny][nx]."""
     return dev_to_abs(gpu.state_get().cpu().numpy(), gpu.consts())
