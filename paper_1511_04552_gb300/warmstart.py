@@ -337,6 +337,38 @@ def evaluate(net, conds, group=64, tol=1e-4, ny=256, nx=256, plain=False):
     return out
 
 
+def perturbed_rest(nx, ny, phi, seed, amp=1e-3):
+    """(u_x, u_y, theta, phi) [4][ny][nx] float32: rest, the conduction profile and phi, plus
+    seeded uniform noise of amplitude amp (amp * phi on phi) from numpy's PCG64 stream."""
+    r = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    out = np.empty((4, ny, nx), dtype=np.float32)
+    out[0] = amp * r.uniform(-1.0, 1.0, (ny, nx))
+    out[1] = amp * r.uniform(-1.0, 1.0, (ny, nx))
+    out[2] = (0.5 - x)[None, :] + amp * r.uniform(-1.0, 1.0, (ny, nx))
+    out[3] = phi * (1.0 + amp * r.uniform(-1.0, 1.0, (ny, nx)))
+    return out
+
+
+def cold_start_spread(conds, n_starts=6, amp=1e-3, ny=256, nx=256, tol=1e-4, seed=0):
+    """How unique the steady hot-wall Nu is: every point of conds [n][3] solved from rest and
+    from n_starts seeded perturbed rest states (perturbed_rest, amplitude amp), all to the same
+    steadiness test. Returns the steady Nu [n][1 + n_starts] (column 0 from rest), the steps,
+    and per point the relative spread (max - min) / median."""
+    import torch
+    n = len(conds)
+    rest = solve_steady(conds, ny, nx, group=n, tol=tol)
+    reps = np.repeat(np.asarray(conds, dtype=np.float64), n_starts, axis=0)
+    warm = [torch.from_numpy(perturbed_rest(nx, ny, float(c[1]), seed * 7919 + k, amp)).cuda()
+            for k, c in enumerate(reps)]
+    pert = solve_steady(reps, ny, nx, warm=warm, group=len(reps), tol=tol)
+    nu = np.concatenate([rest["nu"][:, None], pert["nu"].reshape(n, n_starts)], axis=1)
+    steps = np.concatenate([rest["steps"][:, None], pert["steps"].reshape(n, n_starts)], axis=1)
+    spread = (nu.max(axis=1) - nu.min(axis=1)) / np.median(nu, axis=1)
+    return dict(nu=nu, steps=steps, spread=spread,
+                wall_s=rest["wall_s"] + pert["wall_s"])
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--train", type=int, default=2000, help="training points")
@@ -362,8 +394,22 @@ def main(argv=None):
                     help="only evaluate these weights on --held-out points (seed --seed + 1)")
     ap.add_argument("--plain", action="store_true",
                     help="with --evaluate: also solve every point cold on its own")
+    ap.add_argument("--spread", type=int, default=0,
+                    help="only measure the cold-start spread of the steady Nu on this many "
+                         "held-out points (seed --seed + 1), --starts perturbed starts each")
+    ap.add_argument("--starts", type=int, default=6)
     a = ap.parse_args(argv)
     log = lambda s: print(s, flush=True)  # noqa: E731
+    if a.spread:
+        held = sample_conditions(a.spread, a.seed + 1)
+        sp = cold_start_spread(held, a.starts, ny=a.size, nx=a.size, tol=a.tol)
+        summary = dict(conds=held.tolist(), **{k: (v.tolist() if isinstance(v, np.ndarray)
+                                                    else v) for k, v in sp.items()})
+        log(json.dumps(summary))
+        if a.report:
+            with open(a.report, "w") as f:
+                json.dump(summary, f)
+        return
     if a.bench_train:
         log(json.dumps(bench_train(a.bench_train, ny=a.size, nx=a.size)))
         return
