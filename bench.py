@@ -415,7 +415,7 @@ def main():
         extras["warm_start"] = warm_start_measure(m, torch)
         torch.cuda.empty_cache()
         # cold start to steady Nu (estimated distance to the steady value <= 1e-4, checks every
-        # 1000 steps; binding.steady_nu_reached)
+        # 1000 steps; mclbm_run_to_steady)
         w2 = workloads.CAVITY_256
         sc = m.Cavity(w2["nx"], w2["ny"], w2["Ra"], w2["Pr"], w2["phi"], w2["d_p"]).init()
         torch.cuda.synchronize()

@@ -270,6 +270,44 @@ const char *mclbm_batch_last_error(const mclbm_batch_t *b);
 /* Releases the batch (not the cavities, not the caller's buffer). Waits for its stream. */
 void mclbm_batch_destroy(mclbm_batch_t *b);
 
+/* ---- steady state ------------------------------------------------------------------------
+ * The paper reports steady states (Sec. 3: the hot-wall Nu of Figs 3, 5-7) without saying when
+ * a run is steady. The test here reads "the distance to the steady hot-wall Nu is at most
+ * tol |Nu|" on the hot-wall Nusselt numbers of successive, equally spaced checks. For every lag
+ * L of lags (in checks) the six values Nu_n, Nu_(n-L), ..., Nu_(n-5L), with the five changes
+ * d_0 (latest) ... d_4, must show one of: (a) |d_0| and |d_1| at most 2e-7 L |Nu_n| (round-off
+ * at the FP32 fixed point); (b) two or more sign flips among the changes with all six values
+ * within tol |Nu_n| / 2 (an oscillation about the limit); (c) the four ratios d_k / d_(k+1) in
+ * [0, 0.99) and within 0.05 of each other, and |d_0| r / (1 - r) <= tol |Nu_n| with r the
+ * largest ratio (the rest of a geometric tail). Several lags keep a settled fast mode from
+ * hiding a slow one that still moves Nu (the particle component's migration). */
+
+/* The test on a history nu_hist[0..n) (oldest first). lags = NULL: {1, 32}; otherwise n_lags
+ * (1..8) lags of at least 1. Returns 1 (steady), 0 (not yet, also with fewer than
+ * 5 max(lags) + 1 values) or MCLBM_EINVAL (NULL nu_hist with n > 0, tol <= 0, bad lags).
+ * Host only: needs no GPU. */
+int mclbm_steady_nu_reached(const double *nu_hist, int64_t n, double tol, const int32_t *lags,
+                            int n_lags);
+
+/* Steps a bound, initialised cavity check_every (>= 1) steps at a time, taking mclbm_nusselt
+ * after each chunk, until the test holds for the hot-wall history of this call or max_steps
+ * have been done. Outputs (each may be NULL): steps done by this call, the last Nusselt numbers,
+ * converged (1 when the test held). Returns MCLBM_OK, MCLBM_EINVAL for bad arguments, or the
+ * first failing mclbm_step / mclbm_nusselt code. Syncs at every check. */
+int mclbm_run_to_steady(mclbm_t *h, double tol, int64_t check_every, int64_t max_steps,
+                        const int32_t *lags, int n_lags, int64_t *steps, double *nu_hot,
+                        double *nu_cold, int *converged);
+
+/* The same for every cavity of a batch (check_every even): a cavity whose history passes the
+ * test leaves the tile table (mclbm_batch_set_active) and keeps its state. Host arrays [n] (may
+ * be NULL): steps[c] = the batch step count at which cavity c became steady, -1 if it did not
+ * within max_steps; nu_hot[c] = its hot-wall Nu at that check (else the last one).
+ * *total_steps (may be NULL) = steps the batch ran. Returns as mclbm_run_to_steady, with the
+ * batch calls' codes. */
+int mclbm_batch_run_to_steady(mclbm_batch_t *b, double tol, int64_t check_every,
+                              int64_t max_steps, const int32_t *lags, int n_lags, int64_t *steps,
+                              double *nu_hot, int64_t *total_steps);
+
 /* Derived constants of the handle. */
 int mclbm_get_consts(const mclbm_t *h, mclbm_consts *out);
 

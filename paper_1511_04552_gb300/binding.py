@@ -134,6 +134,15 @@ def lib():
         L.mclbm_batch_last_error.restype = C.c_char_p
         L.mclbm_batch_destroy.argtypes = [vp]
         L.mclbm_batch_destroy.restype = None
+        ip, i64p = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+        L.mclbm_steady_nu_reached.argtypes = [dp, C.c_int64, C.c_double, ip, C.c_int]
+        L.mclbm_steady_nu_reached.restype = C.c_int
+        L.mclbm_run_to_steady.argtypes = [vp, C.c_double, C.c_int64, C.c_int64, ip, C.c_int,
+                                          i64p, dp, dp, C.POINTER(C.c_int)]
+        L.mclbm_run_to_steady.restype = C.c_int
+        L.mclbm_batch_run_to_steady.argtypes = [vp, C.c_double, C.c_int64, C.c_int64, ip,
+                                                C.c_int, i64p, dp, i64p]
+        L.mclbm_batch_run_to_steady.restype = C.c_int
         for name in ("mclbm_batch_create", "mclbm_batch_step", "mclbm_batch_nusselt",
                      "mclbm_batch_set_active", "mclbm_batch_tune"):
             getattr(L, name).restype = C.c_int
@@ -359,72 +368,38 @@ class Cavity:
         return t
 
 
-def _geometric_tail_ok(pts, tol, floor, spread):
-    """pts: six values, latest first, equally spaced. See steady_nu_reached."""
-    nu = pts[0]
-    d = [pts[k] - pts[k + 1] for k in range(5)]  # d[0] is the latest change
-    lim = floor * abs(nu)
-    if abs(d[0]) <= lim and abs(d[1]) <= lim:
-        return True
-    # an oscillation about the limit: the sign of the change flips at least twice and the six
-    # values lie within half the tolerance
-    flips = sum(1 for k in range(4) if d[k] * d[k + 1] < 0.0)
-    if flips >= 2 and max(pts) - min(pts) <= 0.5 * tol * abs(nu):
-        return True
-    if any(x == 0.0 for x in d[1:]):
-        return False
-    r = [d[k] / d[k + 1] for k in range(4)]
-    if not all(0.0 <= x < 0.99 for x in r) or max(r) - min(r) > spread:
-        return False
-    rm = max(r)
-    return abs(d[0]) * rm / (1.0 - rm) <= tol * abs(nu)
-
-
 STRICT_LAGS = (1, 32)
 
 
-def steady_nu_reached(hist, tol=1e-4, lags=STRICT_LAGS, floor=2e-7, spread=0.05):
-    """Steadiness test on the hot-wall Nusselt numbers of successive checks (equal step spacing).
+def _lags(lags):
+    arr = (C.c_int32 * len(lags))(*[int(x) for x in lags])
+    return arr, len(lags)
 
-    For every lag L in `lags` (in checks), the six values Nu_n, Nu_(n-L), ..., Nu_(n-5L) must
-    pass: the five changes have one sign and shrink geometrically with a consistent ratio (four
-    ratios in [0, 0.99) within `spread` of each other, as on the exponential tail of a
-    relaxation) and the tail of that series, |d_n| r / (1 - r) with the largest ratio, is within
-    tol * |Nu|; or the last two changes are below floor * L * |Nu| (the FP32 state at its fixed
-    point: changes are round-off); or Nu oscillates (two or more sign flips) within half the
-    tolerance. A change-below-tolerance test alone also stops where the transient has an
-    extremum. One lag alone is fooled where a faster mode dominates the short-lag changes while a
-    slow one (here the particle component's migration, over 1e5-1e6 steps) still moves Nu: on
-    256^2 cavities, lag 1 alone stopped up to 1.7e-3 away from the Nu reached 1.5 M steps later,
-    lags (1, 32) at most 8.4e-5."""
-    need = 5 * max(lags) + 1
-    if len(hist) < need:
-        return False
-    for L in lags:
-        pts = [hist[-1 - k * L] for k in range(6)]
-        if not _geometric_tail_ok(pts, tol, floor * L, spread):
-            return False
-    return True
+
+def steady_nu_reached(hist, tol=1e-4, lags=STRICT_LAGS):
+    """mclbm_steady_nu_reached: is the hot-wall Nusselt history (oldest first, equally spaced
+    checks) steady to tol on every lag (in checks)? The test is stated in include/mclbm.h."""
+    h = np.ascontiguousarray(np.asarray(hist, dtype=np.float64))
+    arr, n_lags = _lags(lags)
+    rc = lib().mclbm_steady_nu_reached(h.ctypes.data_as(C.POINTER(C.c_double)), h.size,
+                                       float(tol), arr, n_lags)
+    if rc < 0:
+        raise MclbmError(rc, "mclbm_steady_nu_reached")
+    return rc == 1
 
 
 def run_to_steady(cav: Cavity, tol=1e-4, check_every=1000, max_steps=3_000_000,
                   lags=STRICT_LAGS):
-    """Advances until the hot-wall Nusselt number is steady to tol (steady_nu_reached, checks
-    `check_every` steps apart). Returns a dict with the step count, the final Nusselt numbers,
-    the history and whether the criterion was met."""
-    hist = []
-    nus = []
-    steps = 0
-    while steps < max_steps:
-        cav.step(check_every)
-        steps += check_every
-        nh, nc = cav.nusselt()
-        hist.append((steps, nh, nc))
-        nus.append(nh)
-        if steady_nu_reached(nus, tol, lags):
-            return dict(steps=steps, nu_hot=nh, nu_cold=nc, history=hist, converged=True)
-    return dict(steps=steps, nu_hot=hist[-1][1] if hist else None,
-                nu_cold=hist[-1][2] if hist else None, history=hist, converged=False)
+    """mclbm_run_to_steady: advances until the hot-wall Nusselt number is steady to tol (checks
+    `check_every` steps apart). Returns the step count, the final Nusselt numbers and whether the
+    test held."""
+    arr, n_lags = _lags(lags)
+    steps, nh, nc, conv = C.c_int64(), C.c_double(), C.c_double(), C.c_int()
+    cav._check(lib().mclbm_run_to_steady(cav.handle, float(tol), int(check_every),
+                                         int(max_steps), arr, n_lags, C.byref(steps),
+                                         C.byref(nh), C.byref(nc), C.byref(conv)),
+               "mclbm_run_to_steady")
+    return dict(steps=steps.value, nu_hot=nh.value, nu_cold=nc.value, converged=bool(conv.value))
 
 
 class Batch:
@@ -491,33 +466,18 @@ class Batch:
 
 def sweep_to_steady(batch: Batch, tol=1e-4, check_every=1000, max_steps=3_000_000,
                     lags=STRICT_LAGS):
-    """Runs every cavity of a batch until its hot-wall Nusselt number is steady to tol
-    (steady_nu_reached); converged cavities leave the tile table. Returns per-cavity step
-    counts and final Nusselt numbers."""
+    """mclbm_batch_run_to_steady: runs every cavity of a batch until its hot-wall Nusselt number
+    is steady to tol; converged cavities leave the tile table. Returns per-cavity step counts
+    (None where the test did not hold) and Nusselt numbers."""
     n = len(batch.cavities)
-    active = [True] * n
-    hist = [[] for _ in range(n)]
-    done_at = [None] * n
-    steps = 0
+    arr, n_lags = _lags(lags)
+    steps = np.zeros(n, dtype=np.int64)
     nu = np.zeros(n)
-    while any(active) and steps < max_steps:
-        batch.step(check_every)
-        steps += check_every
-        hot, _ = batch.nusselt()
-        changed = False
-        for c in range(n):
-            if not active[c]:
-                continue
-            hist[c].append(hot[c])
-            if steady_nu_reached(hist[c], tol, lags):
-                active[c] = False
-                done_at[c] = steps
-                nu[c] = hot[c]
-                changed = True
-        if changed and any(active):
-            batch.set_active(active)
-    for c in range(n):
-        if done_at[c] is None:
-            nu[c] = hist[c][-1] if hist[c] else np.nan
-    return dict(steps=done_at, nu_hot=nu, total_steps=steps,
-                converged=all(d is not None for d in done_at))
+    total = C.c_int64()
+    batch._check(lib().mclbm_batch_run_to_steady(
+        batch._h, float(tol), int(check_every), int(max_steps), arr, n_lags,
+        steps.ctypes.data_as(C.POINTER(C.c_int64)), nu.ctypes.data_as(C.POINTER(C.c_double)),
+        C.byref(total)), "mclbm_batch_run_to_steady")
+    done = [int(x) if x >= 0 else None for x in steps]
+    return dict(steps=done, nu_hot=nu, total_steps=total.value,
+                converged=all(d is not None for d in done))

@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libmclbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mclbm_step_f32.cu", "mclbm_step_f16.cu", "mclbm_step_bf16.cu", "mclbm_kernels.cu",
            "mclbm_abi.cu", "mclbm_model.cpp", "mclbm_noalloc.cu", "mclbm_batch.cu",
-           "net_gemm.cu", "net_kernels.cu", "net_abi.cu", "mclbm_selftest.cu"]
+           "net_gemm.cu", "net_kernels.cu", "net_abi.cu", "mclbm_selftest.cu", "mclbm_steady.cpp"]
 
 
 def nvcc() -> str:

@@ -630,6 +630,11 @@ struct mclbm_batch {
   char err[512] = {0};
 };
 
+
+namespace mcl {
+int batch_size(const mclbm_batch_t* b) { return b ? (int)b->cav.size() : 0; }
+}  // namespace mcl
+
 namespace {
 
 int bfail(mclbm_batch_t* b, int code, const char* fmt, ...) {

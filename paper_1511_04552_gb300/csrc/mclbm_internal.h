@@ -154,5 +154,6 @@ cudaError_t prepare_batch(int storage, int* per_sm);
 void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
                       const std::vector<int>& active, int order, std::vector<uint32_t>* out);
 constexpr int kBatchTileW = 64;  // batch tiles: 64 x 8 (two nodes per thread)
+int batch_size(const mclbm_batch_t* b);  // cavities of the batch (0 for NULL)
 
 }  // namespace mcl

@@ -158,12 +158,10 @@ __global__ void final_reduce_kernel(const double* __restrict__ partials, int cou
   block_reduce_store<kRedWidth>(acc, red);
 }
 
-// Wall gradients from the theta deviations: with theta = theta_c + theta',
-// (8 T_h - 9 theta_0 + theta_1)/3 = 1/nx + (theta'_1 - 9 theta'_0)/3 and the cold-wall twin
-// (9 theta_{n-1} - theta_{n-2} - 8 T_c)/3 = 1/nx + (9 theta'_{n-1} - theta'_{n-2})/3.
-// Wall gradients from the theta deviations: with theta = theta_c + theta',
-// (8 T_h - 9 theta_0 + theta_1)/3 = 1/nx + (theta'_1 - 9 theta'_0)/3 and the cold-wall twin
-// (9 theta_{n-1} - theta_{n-2} - 8 T_c)/3 = 1/nx + (9 theta'_{n-1} - theta'_{n-2})/3.
+// Wall gradients from the theta deviations (the Eq 33 mixture's with two sets): with
+// theta = theta_c + theta', (8 T_h - 9 theta_0 + theta_1)/3 = 1/nx + (theta'_1 - 9 theta'_0)/3
+// and the cold-wall twin (9 theta_{n-1} - theta_{n-2} - 8 T_c)/3
+// = 1/nx + (9 theta'_{n-1} - theta'_{n-2})/3.
 template <class T>
 __global__ void nusselt_kernel(const T* __restrict__ src, const Layout L, const StepConsts k,
                                double* __restrict__ red) {

@@ -2,7 +2,7 @@
 independence (the paper settles on 160 x 160 before its runs), the aspect ratio of the cavity
 (Section 3.e) and the slip-mechanism ablation (each force of Table 1 switched off in turn, the
 drag always on: without it the explicit forcing of the interaction is unstable at these drag
-rates). Every point is run to the steady hot-wall Nusselt number (binding.steady_nu_reached).
+rates). Every point is run to the steady hot-wall Nusselt number (mclbm_batch_run_to_steady).
 
     python -m paper_1511_04552_gb300.studies [--only grid|aspect|ablation] [--out studies.json]
 """

@@ -1,4 +1,5 @@
-"""Host logic of the steady-Nusselt test (binding.steady_nu_reached) on synthetic histories."""
+"""The steady-Nusselt test (mclbm_steady_nu_reached in the C library, called through the
+binding) on synthetic histories; no GPU needed."""
 import numpy as np
 
 from paper_1511_04552_gb300.binding import steady_nu_reached
@@ -77,3 +78,64 @@ def test_ablation_cases_keep_drag_and_buoyancy():
     for m in masks:
         assert m & B.F_DRAG and m & B.F_BUOYANCY and 0 < m <= B.F_ALL
     assert sorted(bin(B.F_ALL ^ m).count("1") for m in masks) == [0, 1, 1, 1, 1, 1]
+
+
+def _restated(hist, tol, lags, floor=2e-7, spread=0.05):
+    """The steadiness test restated from its definition (include/mclbm.h), independently of the
+    library's code: for every lag, the six values 0, L, ..., 5L checks back."""
+    if len(hist) < 5 * max(lags) + 1:
+        return False
+    for L in lags:
+        p = [hist[-1 - k * L] for k in range(6)]
+        d = [p[k] - p[k + 1] for k in range(5)]
+        nu = abs(p[0])
+        if abs(d[0]) <= floor * L * nu and abs(d[1]) <= floor * L * nu:
+            continue
+        flips = sum(d[k] * d[k + 1] < 0 for k in range(4))
+        if flips >= 2 and max(p) - min(p) <= 0.5 * tol * nu:
+            continue
+        if any(x == 0.0 for x in d[1:]):
+            return False
+        r = [d[k] / d[k + 1] for k in range(4)]
+        if min(r) < 0.0 or max(r) >= 0.99 or max(r) - min(r) > spread:
+            return False
+        if abs(d[0]) * max(r) / (1.0 - max(r)) > tol * nu:
+            return False
+    return True
+
+
+def test_library_test_matches_its_definition_on_random_histories():
+    """mclbm_steady_nu_reached against the restated definition on every prefix of random
+    histories: relaxations with one or two modes, noise at and above the round-off floor,
+    damped and persistent oscillations, several tolerances and lag sets."""
+    rng = np.random.default_rng(11)
+    t = np.arange(260, dtype=np.float64)
+    for case in range(60):
+        kind = case % 4
+        nu0 = rng.uniform(1.0, 8.0)
+        if kind == 0:
+            seq = nu0 + rng.uniform(-1, 1) * rng.uniform(0.8, 0.99) ** t
+        elif kind == 1:
+            seq = (nu0 + rng.uniform(-1, 1) * np.exp(-t / rng.uniform(2, 10))
+                   + rng.uniform(-3e-3, 3e-3) * np.exp(-t / rng.uniform(50, 400)))
+        elif kind == 2:
+            seq = nu0 + rng.uniform(1e-9, 1e-5) * rng.standard_normal(t.size) * nu0
+        else:
+            seq = nu0 + rng.uniform(1e-6, 1e-3) * np.sin(rng.uniform(0.3, 2.5) * t) * \
+                np.exp(-t / rng.uniform(50, 5000)) * nu0
+        tol = [1e-4, 1e-3, 1e-5][case % 3]
+        lags = [(1, 32), (1,), (1, 4, 16)][(case // 3) % 3]
+        for n in range(1, t.size + 1):
+            h = list(seq[:n])
+            assert steady_nu_reached(h, tol, lags) == _restated(h, tol, lags), (case, n)
+
+
+def test_bad_arguments_are_refused():
+    from paper_1511_04552_gb300.binding import MclbmError
+    for kw in (dict(tol=0.0), dict(tol=-1.0), dict(lags=()), dict(lags=(0,)), dict(lags=(1,) * 9)):
+        try:
+            steady_nu_reached([1.0] * 10, **kw)
+        except MclbmError as e:
+            assert e.code == -1
+        else:
+            raise AssertionError(kw)
