@@ -25,6 +25,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads  # noqa: E402
 
 METRIC = "MLUPS & HBM GB/s fraction per MCLBM step; wall time to steady Nu (1e-4)"
@@ -55,6 +57,9 @@ def parse():
                     help="time steps per benchmark step (default: one 1000-step check interval)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (16-bit: stochastic rounding, FP32 arithmetic)")
+    ap.add_argument("--sweep-to-steady", action="store_true",
+                    help="only run the 80-cavity sweep to steady Nu, batched and cavity by cavity, "
+                         "and print that comparison (minutes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 1024^2 roofline case, the steady-Nu run and the CPU baseline")
     return ap.parse_args()
@@ -272,6 +277,45 @@ def sweep_measure(m, torch, steps=1000, tune_steps=64):
             "autotuned": {"tile_order": order, "ctas_per_sm": per_sm}}
 
 
+def sweep_to_steady_measure(m, torch, tol=1e-4, check_every=1000, max_steps=3_000_000):
+    """The 80-cavity parametric sweep run to the steady hot-wall Nu (tol, two-lag test), once
+    batched (autotuned persistent launches, converged cavities leaving the tile table) and once
+    cavity by cavity with their own launches, one after another. Lattice updates counted per
+    cavity up to its own steady step; wall time on the host around each whole solve."""
+    sw = workloads.sweep80()
+    nodes = np.array([c["nx"] * c["ny"] for c in sw], dtype=np.float64)
+    cavs = [m.Cavity(c["nx"], c["ny"], c["Ra"], c["Pr"], c["phi"], c["d_p"]).init() for c in sw]
+    batch = m.Batch(cavs)
+    order, per_sm = batch.tune(2)
+    for c in cavs:  # the tuner's trial steps are real steps: start again from rest
+        c.init()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rb = m.sweep_to_steady(batch, tol=tol, check_every=check_every, max_steps=max_steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    batch.close()
+    steps_b = np.array([s if s is not None else rb["total_steps"] for s in rb["steps"]], float)
+    t0 = time.perf_counter()
+    rs = [m.run_to_steady(c.init(), tol=tol, check_every=check_every, max_steps=max_steps)
+          for c in cavs]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    steps_s = np.array([r["steps"] for r in rs], float)
+    nu_b, nu_s = np.asarray(rb["nu_hot"]), np.array([r["nu_hot"] for r in rs])
+    return {"workload": "sweep80 to steady Nu (%g, two-lag test, checks every %d steps)" % (
+                tol, check_every),
+            "cavities": len(sw), "nodes": int(nodes.sum()),
+            "autotuned": {"tile_order": order, "ctas_per_sm": per_sm},
+            "batched": {"wall_s": t_batch, "mlups": float((nodes * steps_b).sum() / t_batch / 1e6),
+                        "converged": rb["converged"], "total_steps": rb["total_steps"]},
+            "sequential": {"wall_s": t_seq, "mlups": float((nodes * steps_s).sum() / t_seq / 1e6),
+                           "converged": all(r["converged"] for r in rs)},
+            "speedup_wall": t_seq / t_batch,
+            "steps_mean": {"batched": float(steps_b.mean()), "sequential": float(steps_s.mean())},
+            "nu_rel_diff_max": float(np.max(np.abs(nu_b - nu_s) / np.abs(nu_s)))}
+
+
 WARMNET = os.path.join(ROOT, "paper_1511_04552_gb300", "weights", "warmnet_256.npz")
 
 
@@ -324,6 +368,10 @@ def main():
 
     pkg_build.build()
     torch.cuda.set_device(local)
+    if args.sweep_to_steady:
+        if rank == 0:
+            print(json.dumps(sweep_to_steady_measure(m, torch)), flush=True)
+        return
     dist = None
     if ws > 1:
         import torch.distributed as dist_mod
