@@ -31,6 +31,7 @@ struct Layer {
   int up;          // src1 is upsampled by 2
   // shapes
   int H, W, Ho, Wo, kin, Kp, splits;
+  int fsplits;  // forward split over K (layers with few output tiles), 1 otherwise
   int64_t w_off, b_off;
   int film_off;  // offset of this layer's (gamma, beta) slice in r, or -1
   // device buffers
@@ -142,7 +143,17 @@ void plan(mclbm_net* n) {
       film_off += 2 * y.cout;
     }
     const int tiles = ((y.cout + 127) / 128) * ((y.Kp + 127) / 128);
-    y.splits = std::max(1, std::min(64, 304 / tiles));
+    // weight gradient split over pixels so that its tiles fill one wave of the persistent GEMM
+    // (one CTA per SM with an MN-major B; 152 SMs on GB300); it changes only the order in which
+    // the FP32 partial sums are added
+    y.splits = std::max(1, std::min(64, 152 / tiles));
+    // forward GEMMs with fewer output tiles than half a wave are split over K as well (partial
+    // sums reduced in a fixed order by the epilogue kernel)
+    const int64_t tiles_f = (((int64_t)c.max_batch * y.Ho * y.Wo + 127) / 128) *
+                            ((y.cout + 127) / 128);
+    const int nks = (y.Kp + 63) / 64;
+    y.fsplits = tiles_f >= 76 ? 1 : (int)std::max<int64_t>(
+                                        1, std::min<int64_t>({152 / tiles_f, 8, (int64_t)nks}));
   }
   n->F = film_off;
   n->mlp_off = off;
@@ -168,6 +179,8 @@ void plan(mclbm_net* n) {
     bytes += align256((size_t)y.cout * B * 3 * 8);           // partial
     if (l > 0) n->dcols_elems = std::max(n->dcols_elems, P * y.Kp);
     n->wpart_elems = std::max(n->wpart_elems, (size_t)y.splits * y.cout * y.Kp);
+    if (y.fsplits > 1)
+      n->wpart_elems = std::max(n->wpart_elems, (size_t)y.fsplits * y.cout * P);
   }
   bytes += align256(n->dcols_elems * 4);
   bytes += align256(n->wpart_elems * 4);
@@ -283,8 +296,6 @@ cudaError_t forward(mclbm_net* n, int batch, const float* cond) {
     g.M = P;
     g.N = y.cout;
     g.K = y.Kp;
-    g.k_per_split = ((y.Kp + 63) / 64) * 64;
-    g.mode = kGemmConvFwd;
     g.ep.bias = n->params + y.b_off;
     g.ep.film = y.film ? n->r : nullptr;
     g.ep.film_stride = n->F;
@@ -294,7 +305,24 @@ cudaError_t forward(mclbm_net* n, int batch, const float* cond) {
     g.ep.y = l == kNumLayers - 1 ? nullptr : y.y;
     g.ep.act = y.act;
     g.err = n->err;
-    if ((e = launch_gemm(g, 1, st)) != cudaSuccess) return e;
+    if (y.fsplits > 1) {
+      // partial products per K split, column-major [split][cout][P], then the epilogue
+      const int nks = (y.Kp + 63) / 64;
+      g.k_per_split = (int64_t)((nks + y.fsplits - 1) / y.fsplits) * 64;
+      g.mode = kGemmRaw;
+      g.d = n->wpart;
+      g.ldd = P;
+      g.d_trans = 1;
+      g.split_stride = (int64_t)y.cout * P;
+      if ((e = launch_gemm(g, y.fsplits, st)) != cudaSuccess) return e;
+      if ((e = launch_conv_epilogue_splitk(n->wpart, y.fsplits, g.split_stride, P, y.cout, g.ep,
+                                           st)) != cudaSuccess)
+        return e;
+    } else {
+      g.k_per_split = ((y.Kp + 63) / 64) * 64;
+      g.mode = kGemmConvFwd;
+      if ((e = launch_gemm(g, 1, st)) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

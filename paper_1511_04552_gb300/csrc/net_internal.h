@@ -50,9 +50,11 @@ struct GemmArgs {
   int mode;
   ConvEpilogue ep;
   int* err;  // bit 0 set when a bounded wait gave up (may be null)
+  int splits;  // set by launch_gemm: K splits (tiles of D are m x n x split)
 };
 
-// Checks the operand requirements and launches grid (ceil(M/128), ceil(N/128), splits).
+// Checks the operand requirements and launches a persistent grid over the ceil(M/128) x
+// ceil(N/128) x splits tiles of D.
 cudaError_t launch_gemm(const GemmArgs& g, int splits, cudaStream_t st);
 // True if the arguments satisfy the alignment and extent rules of launch_gemm.
 bool gemm_args_valid(const GemmArgs& g, int splits);
@@ -101,6 +103,12 @@ cudaError_t launch_bias_film_grad(const double* partial, int C, int batch, float
 // grad[o][k] = sum_z part[z][o][k] for k < kin (dropping padding columns up to Kp).
 cudaError_t launch_splitk_reduce(const float* part, int splits, int64_t split_stride, int C,
                                  int kin, int Kp, float* grad, cudaStream_t st);
+
+// The convolution epilogue after a K-split forward GEMM: part [splits][N][M] (column-major
+// partial products, split_stride apart) summed over the splits in order, then bias, FiLM and the
+// activation as the GEMM's own epilogue applies them (pre and y [N][M]).
+cudaError_t launch_conv_epilogue_splitk(const float* part, int splits, int64_t split_stride,
+                                        int M, int N, const ConvEpilogue& e, cudaStream_t st);
 
 // W [C][kin] FP32 -> wb [C][Kp] BF16 (round to nearest, zero padding).
 cudaError_t launch_weights_bf16(const float* w, int C, int kin, int Kp, __nv_bfloat16* wb,

@@ -191,6 +191,26 @@ __global__ void splitk_reduce_kernel(const float* part, int splits, int64_t spli
   }
 }
 
+__global__ void conv_epilogue_splitk_kernel(const float* __restrict__ part, int splits,
+                                            int64_t split_stride, int M, int N,
+                                            const ConvEpilogue e) {
+  const int64_t n = (int64_t)N * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(t / M), row = (int)(t % M);
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[z * split_stride + t];
+    const float pre = s + e.bias[o];
+    float zz = pre;
+    if (e.film) {
+      const float* f = e.film + (int64_t)(row / e.hw) * e.film_stride + e.film_off;
+      zz = (1.f + f[o]) * pre + f[N + o];
+    }
+    e.pre[t] = pre;
+    if (e.y) e.y[t] = e.act ? zz / (1.f + expf(-zz)) : zz;
+  }
+}
+
 __global__ void weights_bf16_kernel(const float* w, int C, int kin, int Kp, __nv_bfloat16* wb) {
   const int64_t n = (int64_t)C * Kp;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -438,6 +458,13 @@ cudaError_t launch_splitk_reduce(const float* part, int splits, int64_t split_st
                                  int kin, int Kp, float* grad, cudaStream_t st) {
   splitk_reduce_kernel<<<grid_for((int64_t)C * kin, 256, 1024), 256, 0, st>>>(
       part, splits, split_stride, C, kin, Kp, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_epilogue_splitk(const float* part, int splits, int64_t split_stride,
+                                        int M, int N, const ConvEpilogue& e, cudaStream_t st) {
+  conv_epilogue_splitk_kernel<<<grid_for((int64_t)N * M, 256, 2048), 256, 0, st>>>(
+      part, splits, split_stride, M, N, e);
   return cudaGetLastError();
 }
 
