@@ -220,7 +220,10 @@ __global__ void weights_bf16_kernel(const float* w, int C, int kin, int Kp, __nv
   }
 }
 
-// ---- conditioning MLP (one block; sizes are tiny) ---------------------------------------------
+// ---- conditioning MLP (sizes are tiny: batch x 3 -> H -> F) -------------------------------------
+// Forward over a grid: every block rebuilds the normalised conditions c and the hidden layer
+// h = SiLU(W1 c + b1) in shared memory (batch x (3 + H) values) and computes its slice of the
+// batch x F outputs r = W2 h + b2; block 0 also stores c and the pre-activations a1.
 __global__ void mlp_forward_kernel(const MlpArgs a) {
   extern __shared__ float sm[];
   float* c = sm;                    // [batch][3]
@@ -232,16 +235,18 @@ __global__ void mlp_forward_kernel(const MlpArgs a) {
     c[3 * t + 2] = (dp * 1e9f - 55.f) / 45.f;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < a.batch * 3; t += blockDim.x) a.c[t] = c[t];
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.batch * 3; t += blockDim.x) a.c[t] = c[t];
   for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) {
     const int b = t / a.H, j = t % a.H;
     const float s = a.b1[j] + a.W1[3 * j] * c[3 * b] + a.W1[3 * j + 1] * c[3 * b + 1] +
                     a.W1[3 * j + 2] * c[3 * b + 2];
-    a.a1[t] = s;
+    if (blockIdx.x == 0) a.a1[t] = s;
     h[t] = silu_f(s);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < a.batch * a.F; t += blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.batch * a.F;
+       t += gridDim.x * blockDim.x) {
     const int b = t / a.F, f = t % a.F;
     float s = a.b2[f];
     for (int j = 0; j < a.H; ++j) s += a.W2[(int64_t)f * a.H + j] * h[b * a.H + j];
@@ -249,41 +254,45 @@ __global__ void mlp_forward_kernel(const MlpArgs a) {
   }
 }
 
-__global__ void mlp_backward_kernel(const MlpArgs a, const float* dr, float* gW1, float* gb1,
-                                    float* gW2, float* gb2) {
-  extern __shared__ float sm[];
-  float* h = sm;                    // [batch][H]
-  float* da1 = sm + a.batch * a.H;  // [batch][H]
-  for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) h[t] = silu_f(a.a1[t]);
-  __syncthreads();
-  for (int t = threadIdx.x; t < a.F * a.H; t += blockDim.x) {
-    const int f = t / a.H, j = t % a.H;
-    float s = 0.f;
-    for (int b = 0; b < a.batch; ++b) s += dr[(int64_t)b * a.F + f] * h[b * a.H + j];
-    gW2[t] = s;
+// Backward, second layer: gW2[f][j] = sum_b dr[b][f] h[b][j], gb2[f] = sum_b dr[b][f] (grid over
+// the F x H + F outputs, sums in batch order).
+__global__ void mlp_backward_w2_kernel(const MlpArgs a, const float* dr, float* gW2, float* gb2) {
+  const int n = a.F * a.H;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n + a.F;
+       t += gridDim.x * blockDim.x) {
+    if (t < n) {
+      const int f = t / a.H, j = t % a.H;
+      float s = 0.f;
+      for (int b = 0; b < a.batch; ++b)
+        s += dr[(int64_t)b * a.F + f] * silu_f(a.a1[b * a.H + j]);
+      gW2[t] = s;
+    } else {
+      const int f = t - n;
+      float s = 0.f;
+      for (int b = 0; b < a.batch; ++b) s += dr[(int64_t)b * a.F + f];
+      gb2[f] = s;
+    }
   }
-  for (int f = threadIdx.x; f < a.F; f += blockDim.x) {
-    float s = 0.f;
-    for (int b = 0; b < a.batch; ++b) s += dr[(int64_t)b * a.F + f];
-    gb2[f] = s;
-  }
-  for (int t = threadIdx.x; t < a.batch * a.H; t += blockDim.x) {
-    const int b = t / a.H, j = t % a.H;
+}
+
+// Backward, first layer: block j computes da1[b][j] = (sum_f W2[f][j] dr[b][f]) SiLU'(a1[b][j])
+// for every b (in f order), then gW1[j][i] = sum_b da1[b][j] c[b][i] and gb1[j] = sum_b da1[b][j]
+// (in batch order).
+__global__ void mlp_backward_w1_kernel(const MlpArgs a, const float* dr, float* gW1, float* gb1) {
+  extern __shared__ float da1[];  // [batch]
+  const int j = blockIdx.x;
+  for (int b = threadIdx.x; b < a.batch; b += blockDim.x) {
     float s = 0.f;
     for (int f = 0; f < a.F; ++f) s += a.W2[(int64_t)f * a.H + j] * dr[(int64_t)b * a.F + f];
-    da1[t] = s * dsilu_f(a.a1[t]);
+    da1[b] = s * dsilu_f(a.a1[b * a.H + j]);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < a.H * 3; t += blockDim.x) {
-    const int j = t / 3, i = t % 3;
+  if (threadIdx.x < 4) {
+    const int i = threadIdx.x;
     float s = 0.f;
-    for (int b = 0; b < a.batch; ++b) s += da1[b * a.H + j] * a.c[3 * b + i];
-    gW1[t] = s;
-  }
-  for (int j = threadIdx.x; j < a.H; j += blockDim.x) {
-    float s = 0.f;
-    for (int b = 0; b < a.batch; ++b) s += da1[b * a.H + j];
-    gb1[j] = s;
+    for (int b = 0; b < a.batch; ++b) s += i < 3 ? da1[b] * a.c[3 * b + i] : da1[b];
+    if (i < 3) gW1[3 * j + i] = s;
+    else gb1[j] = s;
   }
 }
 
@@ -476,14 +485,17 @@ cudaError_t launch_weights_bf16(const float* w, int C, int kin, int Kp, __nv_bfl
 
 cudaError_t launch_mlp_forward(const MlpArgs& a, cudaStream_t st) {
   const size_t sm = sizeof(float) * (size_t)a.batch * (3 + a.H);
-  mlp_forward_kernel<<<1, 256, sm, st>>>(a);
+  mlp_forward_kernel<<<grid_for((int64_t)a.batch * a.F, 256, 152), 256, sm, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_backward(const MlpArgs& a, const float* dr, float* gW1, float* gb1,
                                 float* gW2, float* gb2, cudaStream_t st) {
-  const size_t sm = sizeof(float) * (size_t)a.batch * a.H * 2;
-  mlp_backward_kernel<<<1, 256, sm, st>>>(a, dr, gW1, gb1, gW2, gb2);
+  mlp_backward_w2_kernel<<<grid_for((int64_t)a.F * a.H + a.F, 256, 304), 256, 0, st>>>(a, dr,
+                                                                                        gW2, gb2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mlp_backward_w1_kernel<<<a.H, 32, sizeof(float) * (size_t)a.batch, st>>>(a, dr, gW1, gb1);
   return cudaGetLastError();
 }
 
