@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,6 +36,7 @@ struct mclbm {
   int* err_dev = nullptr;       // device error word of the step kernels (bounded waits)
   uint32_t* epoch = nullptr;    // graph replay counter seeding 16-bit stochastic rounding
   CUtensorMap tmap[2];          // two-level state for the TMA step kernel: loads, stores
+  CUtensorMap tmap2;            // two-level state for the two-step kernel's window loads
   int cur = 0;
   bool initialised = false;
   bool diverged = false;
@@ -131,8 +133,15 @@ int build_graph(mclbm_t* h, int from) {
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
-  for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
-    le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, h->tmap, h->cap_stream);
+  if (h->cfg.two) {  // pairs of steps: kGraphSteps / 2 launches, the level alternating per pair
+    for (int s = 0; s < kGraphSteps / 2 && le == cudaSuccess; ++s)
+      le = launch_two_f32(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, &h->tmap2,
+                          h->cap_stream);
+  } else {
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
+      le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, h->tmap,
+                       h->cap_stream);
+  }
   // a new stochastic-rounding epoch for the next replay
   if (le == cudaSuccess) le = launch_epoch_advance(h->epoch, h->cap_stream);
   cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
@@ -280,6 +289,19 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
       h->cfg.variant = 0;
     }
   }
+  // MCLBM_STEP_VARIANT = two (FP32 lattices of at most one 32 x 16 tile per SM): pairs of steps
+  // in one launch, bitwise the same states; not the default, since it is no faster (the first
+  // step's 1.7x redundant work outweighs the launch it saves)
+  const char* sv = std::getenv("MCLBM_STEP_VARIANT");
+  const bool two_asked = sv && std::strcmp(sv, "two") == 0;
+  if (two_asked && h->cfg.variant == 2 && h->L.storage == MCLBM_STORE_F32 &&
+      h->L.np == kPlanes && h->cfg.vec != 2) {
+    if (prepare_two_f32(&h->cfg, h->L) != cudaSuccess ||
+        make_two_step_tensor_map(&h->tmap2, h->state[0], h->L) != cudaSuccess) {
+      cudaGetLastError();
+      h->cfg.two = false;
+    }
+  }
   CK(h, cudaMemsetAsync(h->err_dev, 0, 2 * sizeof(int), h->stream));
   h->cur = 0;
   h->initialised = false;
@@ -320,6 +342,12 @@ int mclbm_step(mclbm_t* h, int64_t n) {
     CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
     left -= kGraphSteps;  // even: the current time level is unchanged
     h->steps += kGraphSteps;
+  }
+  for (; h->cfg.two && left >= 2; left -= 2) {  // a pair of steps moves to the other level
+    CK(h, launch_two_f32(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg,
+                         &h->tmap2, h->stream));
+    h->cur ^= 1;
+    h->steps += 2;
   }
   for (; left > 0; --left) {
     CK(h, launch_step(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg, h->tmap,

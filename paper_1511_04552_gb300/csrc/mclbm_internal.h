@@ -81,6 +81,8 @@ struct StepConfig {
   int grid;     // TMA kernel: persistent CTAs (set by prepare_step)
   bool sr;      // 16-bit storage: stochastic rounding (else round to nearest)
   int vec;      // nodes per thread of the step kernels: 1 or 2 (0: chosen by lattice size)
+  bool two;     // FP32: pairs of steps by the two-step kernel (set by prepare_two_f32)
+  int grid2;    // two-step kernel: CTAs (one per 32 x 16 tile)
 };
 StepConfig choose_step_config(int nx, int ny, int np);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
@@ -90,6 +92,13 @@ cudaError_t prepare_step(StepConfig* c, const Layout& L);
 // with tiles tile_w x 8: maps[0] loads input windows (the tile with 16 bytes of columns and 2
 // rows of halo on each side), maps[1] stores output tiles.
 cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w);
+// The two-step kernel's window loads (FP32): 32 x 16 tiles with 4 nodes of halo on each side.
+cudaError_t make_two_step_tensor_map(CUtensorMap* map, void* state0, const Layout& L);
+// Two-step kernel (FP32 storage): enables it in c when every SM can take one 32 x 16 tile
+// (cudaErrorNotSupported otherwise); launches one two-step launch from a.src to a.dst.
+cudaError_t prepare_two_f32(StepConfig* c, const Layout& L);
+cudaError_t launch_two_f32(const StepArgs& a, const StepConfig& c, const CUtensorMap* map2,
+                           cudaStream_t st);
 // Tile width of a configured step kernel's TMA maps.
 int step_tile_width(const StepConfig& c);
 cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMap* map,

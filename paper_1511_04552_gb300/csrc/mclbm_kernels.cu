@@ -303,9 +303,11 @@ StepConfig choose_step_config(int nx, int ny, int np) {
   c.variant = (nx >= 64 && ny >= 32) ? 2 : 0;
   const char* v = std::getenv("MCLBM_STEP_VARIANT");
   if (v && std::strcmp(v, "tile") == 0) c.variant = 0;
-  if (v && std::strcmp(v, "tma") == 0) c.variant = 2;
+  if (v && (std::strcmp(v, "tma") == 0 || std::strcmp(v, "two") == 0)) c.variant = 2;
   c.grid = 0;
   c.sr = true;
+  c.two = false;
+  c.grid2 = 0;
   // MCLBM_STEP_VEC = 1 | 2 forces the nodes per thread (comparisons; default by lattice size)
   const char* vv = std::getenv("MCLBM_STEP_VEC");
   c.vec = (vv && (vv[0] == '1' || vv[0] == '2') && vv[1] == 0) ? vv[0] - '0' : 0;
@@ -386,6 +388,29 @@ cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout&
   r = encode(&maps[1], dt, 3, state0, dims, strides, tile, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_two_step_tensor_map(CUtensorMap* map, void* state0, const Layout& L) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if (L.storage != MCLBM_STORE_F32 || L.np != kPlanes) return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)(2 * kPlanes)};
+  const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+  const cuuint32_t box[3] = {32 + 2 * 4, 16 + 2 * 4, (cuuint32_t)kPlanes};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, state0, dims, strides, box,
+                            elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -254,6 +254,33 @@ def test_step_variants_bitwise_identical(nx, ny, storage, monkeypatch):
         assert (a[9 * g:9 * g + 9] - b[9 * g:9 * g + 9]).norm() <= tol * den, g
 
 
+@pytest.mark.parametrize("nx,ny,mask,steps", [
+    (64, 32, 127, 131),     # one graph of 64 steps as 32 pairs, pairs, and an odd last step
+    (256, 256, 127, 67),    # the benchmark lattice: 128 tiles of 32 x 16
+    (130, 35, 127, 64),     # ragged tiles both ways
+    (200, 67, 4 | 8 | 16 | 64, 66),  # masked forces (the general build)
+    (100, 100, 127, 2),     # one pair
+])
+def test_two_step_kernel_equals_single_steps(nx, ny, mask, steps, monkeypatch):
+    """The two-step kernel (MCLBM_STEP_VARIANT=two; FP32 lattices of at most one 32 x 16 tile
+    per SM) runs pairs of steps in one launch, the first step on the tile's 36 x 20
+    surroundings kept in shared memory; the states equal those of single steps with one node
+    per thread bit for bit."""
+    import torch
+    import paper_1511_04552_gb300 as m
+    monkeypatch.setenv("MCLBM_STEP_VARIANT", "two")
+    monkeypatch.delenv("MCLBM_STEP_VEC", raising=False)
+    two = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9, force_mask=mask).init()
+    two.step(steps)
+    monkeypatch.setenv("MCLBM_STEP_VARIANT", "tma")
+    monkeypatch.setenv("MCLBM_STEP_VEC", "1")
+    one = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9, force_mask=mask).init()
+    one.step(steps)
+    assert two.steps_done() == one.steps_done() == steps
+    assert torch.equal(two.state_get(), one.state_get())
+    assert two.nusselt() == one.nusselt()
+
+
 def test_warm_init_with_density_matches_oracle():
     """MCLBM_INIT_WARM_RHO (ux, uy, theta, phi, rho^w) against the oracle's same init, then 500
     steps."""
