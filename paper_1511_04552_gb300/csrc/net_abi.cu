@@ -32,11 +32,14 @@ struct Layer {
   // shapes
   int H, W, Ho, Wo, kin, Kp, splits;
   int fsplits;  // forward split over K (layers with few output tiles), 1 otherwise
+  // input gradient as a convolution of the output gradient (stride 1, 9 cout <= Kp): the
+  // flipped, transposed kernel wt [cin][kp2], kp2 = 9 cout rounded up to 8
+  int tconv, kp2;
   int64_t w_off, b_off;
   int film_off;  // offset of this layer's (gamma, beta) slice in r, or -1
   // device buffers
   float *pre, *y, *dy;
-  __nv_bfloat16 *cols, *wb, *dpre;
+  __nv_bfloat16 *cols, *wb, *dpre, *wt;
   double* partial;
 };
 
@@ -133,6 +136,8 @@ void plan(mclbm_net* n) {
     y.Wo = y.W / y.stride;
     y.kin = 9 * (y.cu + y.cs);
     y.Kp = (y.kin + 7) & ~7;
+    y.kp2 = (9 * y.cout + 7) & ~7;
+    y.tconv = l > 0 && y.stride == 1 && y.kp2 <= y.Kp;
     y.w_off = off;
     off += (int64_t)y.cout * y.kin;
     y.b_off = off;
@@ -175,6 +180,7 @@ void plan(mclbm_net* n) {
     bytes += 3 * align256((size_t)y.cout * P * 4);           // pre, y, dy
     bytes += align256(P * y.Kp * 2);                         // cols
     bytes += align256((size_t)y.cout * y.Kp * 2);            // wb
+    if (y.tconv) bytes += align256((size_t)(y.cu + y.cs) * y.kp2 * 2);  // wt
     bytes += align256((size_t)y.cout * P * 2);               // dpre
     bytes += align256((size_t)y.cout * B * 3 * 8);           // partial
     if (l > 0) n->dcols_elems = std::max(n->dcols_elems, P * y.Kp);
@@ -217,6 +223,7 @@ void assign(mclbm_net* n) {
     y.dy = carve<float>(p, (size_t)y.cout * P);
     y.cols = carve<__nv_bfloat16>(p, P * y.Kp);
     y.wb = carve<__nv_bfloat16>(p, (size_t)y.cout * y.Kp);
+    y.wt = y.tconv ? carve<__nv_bfloat16>(p, (size_t)(y.cu + y.cs) * y.kp2) : nullptr;
     y.dpre = carve<__nv_bfloat16>(p, (size_t)y.cout * P);
     y.partial = carve<double>(p, (size_t)y.cout * B * 3);
   }
@@ -257,6 +264,10 @@ cudaError_t refresh_bf16_weights(mclbm_net* n) {
     const Layer& y = n->L[l];
     cudaError_t e = launch_weights_bf16(n->params + y.w_off, y.cout, y.kin, y.Kp, y.wb, n->stream);
     if (e != cudaSuccess) return e;
+    if (y.tconv &&
+        (e = launch_weights_t_bf16(n->params + y.w_off, y.cout, y.cu + y.cs, y.kp2, y.wt,
+                                   n->stream)) != cudaSuccess)
+      return e;
   }
   return cudaSuccess;
 }
@@ -389,6 +400,57 @@ cudaError_t loss_backward(mclbm_net* n, int batch, const float* cond, const floa
                                   n->grads + y.w_off, st)) != cudaSuccess)
       return e;
     if (l == 0) break;
+    if (y.tconv) {
+      // input gradient of a stride-1 convolution as the convolution of the output gradient with
+      // the flipped, transposed kernel: dX[c][q] = sum_(o, t) wt[c][o 9 + t] cols2[q][o 9 + t],
+      // cols2 the im2col rows of dpre (in this layer's cols buffer), then routed to the sources
+      Im2colBf16Args ib;
+      ib.src = y.dpre;
+      ib.C = y.cout;
+      ib.batch = batch;
+      ib.H = y.Ho;
+      ib.W = y.Wo;
+      ib.Kp = y.kp2;
+      ib.cols = y.cols;
+      if ((e = launch_im2col_bf16(ib, st)) != cudaSuccess) return e;
+      std::memset(&g, 0, sizeof(g));
+      g.a = y.cols;
+      g.lda = y.kp2;
+      g.a_kmajor = 1;
+      g.b = y.wt;
+      g.ldb = y.kp2;
+      g.b_kmajor = 1;
+      g.M = P;
+      g.N = y.cu + y.cs;
+      g.K = y.kp2;
+      g.k_per_split = ((y.kp2 + 63) / 64) * 64;
+      g.d = n->dcols;
+      g.ldd = P;
+      g.d_trans = 1;
+      g.mode = kGemmRaw;
+      g.err = n->err;
+      if ((e = launch_gemm(g, 1, st)) != cudaSuccess) return e;
+      RouteArgs ra;
+      ra.dx = n->dcols;
+      ra.cu = y.cu;
+      ra.cs = y.src2 >= 0 ? y.cs : 0;
+      ra.up = y.up;
+      ra.batch = batch;
+      ra.H = y.H;
+      ra.W = y.W;
+      ra.dsrc1 = n->L[y.src1].dy;
+      ra.acc1 = written[y.src1] ? 1 : 0;
+      written[y.src1] = true;
+      ra.dsrc2 = nullptr;
+      ra.acc2 = 0;
+      if (y.src2 >= 0) {
+        ra.dsrc2 = n->L[y.src2].dy;
+        ra.acc2 = written[y.src2] ? 1 : 0;
+        written[y.src2] = true;
+      }
+      if ((e = launch_route_grad(ra, st)) != cudaSuccess) return e;
+      continue;
+    }
     // input gradient: dcols[k][p] = sum_o dpre[o][p] wb[o][k], stored column-major so that
     // the epilogue's stores and col2im's reads are coalesced over pixels
     std::memset(&g, 0, sizeof(g));

@@ -71,6 +71,32 @@ struct Im2colArgs {
 };
 cudaError_t launch_im2col(const Im2colArgs& a, cudaStream_t st);
 
+// im2col of a BF16 tensor [C][batch * H * W] for a stride-1 3 x 3 convolution with zero
+// padding: cols [batch * H * W][Kp], column c * 9 + tap (tap = 3 ky + kx), zero beyond 9 C.
+struct Im2colBf16Args {
+  const __nv_bfloat16* src;
+  int C, batch, H, W, Kp;
+  __nv_bfloat16* cols;
+};
+cudaError_t launch_im2col_bf16(const Im2colBf16Args& a, cudaStream_t st);
+
+// W [cout][9 cin] FP32 -> the input-gradient operand wt [cin][Kp2] BF16 (round to nearest, as
+// wb): wt[c][o 9 + t] = W[o][c 9 + 8 - t], the flipped and transposed kernel; zero beyond 9 cout.
+cudaError_t launch_weights_t_bf16(const float* w, int cout, int cin, int Kp2, __nv_bfloat16* wt,
+                                  cudaStream_t st);
+
+// dX [cu + cs][P] (P = batch * H * W, the convolution's input grid) to its sources' gradients:
+// channels [0, cu) to dsrc1 (summed over each 2 x 2 block, in row order, when src1 was upsampled
+// by 2), [cu, cu + cs) to dsrc2; each written (acc = 0) or added to (acc = 1).
+struct RouteArgs {
+  const float* dx;
+  int cu, cs, up, batch, H, W;
+  float* dsrc1;
+  float* dsrc2;
+  int acc1, acc2;
+};
+cudaError_t launch_route_grad(const RouteArgs& a, cudaStream_t st);
+
 // Gradient with respect to one source of a convolution's input from dcols [Kp][P] (FP32,
 // column k = c * 9 + tap of the im2col matrix stored contiguously over the P output pixels):
 // channels [c_lo, c_lo + C) of the concatenated input, source grid Hs x Ws (H/2 if up).

@@ -85,6 +85,82 @@ __global__ void im2col_kernel(const Im2colArgs a) {
   }
 }
 
+// ---- input gradient as a convolution (stride-1 layers) --------------------------------------
+__global__ void im2col_bf16_kernel(const Im2colBf16Args a) {
+  const int kg_n = a.Kp / 8;
+  const int64_t P = (int64_t)a.batch * a.H * a.W;
+  const int kin = 9 * a.C;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * kg_n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int kg = (int)(t % kg_n);
+    const int64_t p = t / kg_n;
+    const int x = (int)(p % a.W);
+    const int y = (int)((p / a.W) % a.H);
+    const int b = (int)(p / ((int64_t)a.W * a.H));
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kg * 8 + j;
+      __nv_bfloat16 s = __float2bfloat16_rn(0.f);
+      if (k < kin) {
+        const int c = k / 9, tap = k - 9 * c;
+        const int yi = y + tap / 3 - 1, xi = x + tap % 3 - 1;
+        if (yi >= 0 && yi < a.H && xi >= 0 && xi < a.W)
+          s = a.src[((int64_t)c * a.batch + b) * a.H * a.W + (int64_t)yi * a.W + xi];
+      }
+      v[j] = s;
+    }
+    *reinterpret_cast<uint4*>(a.cols + p * a.Kp + kg * 8) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+__global__ void weights_t_bf16_kernel(const float* w, int cout, int cin, int Kp2,
+                                      __nv_bfloat16* wt) {
+  const int64_t n = (int64_t)cin * Kp2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / Kp2), k = (int)(t % Kp2);
+    float v = 0.f;
+    if (k < 9 * cout) {
+      const int o = k / 9, tap = k - 9 * o;
+      v = w[(int64_t)o * 9 * cin + c * 9 + (8 - tap)];
+    }
+    wt[t] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void route_grad_kernel(const RouteArgs a) {
+  const int64_t hw = (int64_t)a.H * a.W;
+  const int Hs = a.up ? a.H / 2 : a.H, Ws = a.up ? a.W / 2 : a.W;
+  const int64_t n1 = (int64_t)a.cu * a.batch * Hs * Ws, n2 = (int64_t)a.cs * a.batch * hw;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n1 + n2;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < n1) {
+      const int xs = (int)(t % Ws);
+      const int ys = (int)((t / Ws) % Hs);
+      const int64_t cb = t / ((int64_t)Ws * Hs);  // c * batch + b
+      const float* d = a.dx + cb * hw;
+      float s;
+      if (a.up) {
+        const int64_t r0 = (int64_t)(2 * ys) * a.W + 2 * xs;
+        s = d[r0];
+        s += d[r0 + 1];
+        s += d[r0 + a.W];
+        s += d[r0 + a.W + 1];
+      } else {
+        s = d[(int64_t)ys * a.W + xs];
+      }
+      if (a.acc1) a.dsrc1[t] += s;
+      else a.dsrc1[t] = s;
+    } else {
+      const int64_t u = t - n1;
+      const float s = a.dx[(int64_t)a.cu * a.batch * hw + u];
+      if (a.acc2) a.dsrc2[u] += s;
+      else a.dsrc2[u] = s;
+    }
+  }
+}
+
 // ---- col2im (gather) ------------------------------------------------------------------------
 // One thread per element of the source: the sum over its (1 or 4) positions in the input grid
 // and over the 3 x 3 taps of the output pixels that read it, in a fixed order.
@@ -441,6 +517,26 @@ cudaError_t launch_uniform_fill(float* p, int64_t n, float scale, uint64_t seed,
 cudaError_t launch_im2col(const Im2colArgs& a, cudaStream_t st) {
   const int64_t n = (int64_t)a.batch * a.Ho * a.Wo * (a.Kp / 8);
   im2col_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_im2col_bf16(const Im2colBf16Args& a, cudaStream_t st) {
+  const int64_t n = (int64_t)a.batch * a.H * a.W * (a.Kp / 8);
+  im2col_bf16_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weights_t_bf16(const float* w, int cout, int cin, int Kp2, __nv_bfloat16* wt,
+                                  cudaStream_t st) {
+  weights_t_bf16_kernel<<<grid_for((int64_t)cin * Kp2, 256, 1024), 256, 0, st>>>(w, cout, cin,
+                                                                                  Kp2, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_route_grad(const RouteArgs& a, cudaStream_t st) {
+  const int Hs = a.up ? a.H / 2 : a.H, Ws = a.up ? a.W / 2 : a.W;
+  const int64_t n = (int64_t)a.cu * a.batch * Hs * Ws + (int64_t)a.cs * a.batch * a.H * a.W;
+  route_grad_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
