@@ -1,6 +1,8 @@
 // CUDA-core kernels of the warm-start network around the tensor-core GEMM (net_gemm.cu):
-// im2col with fused nearest upsampling and channel concatenation, its adjoint (col2im as a
-// gather, so every input gradient is summed in a fixed order), the backward of FiLM + SiLU with
+// im2col with fused nearest upsampling and channel concatenation, the input gradient of the
+// stride-1 layers as a convolution (im2col of the output gradient, the flipped kernel, routing
+// to the sources) and of the stride-2 layers by col2im as a gather (every input gradient summed
+// in a fixed order), the backward of FiLM + SiLU with
 // the per-channel reductions, the conditioning MLP, the loss, Adam, and small helpers.
 // Activations are channel-major: x[c][b * H * W + y * W + x].
 #include <cuda_bf16.h>
