@@ -87,6 +87,46 @@ __global__ void im2col_kernel(const Im2colArgs a) {
   }
 }
 
+// Channel counts in multiples of 8 (every layer but the geometry input): one thread per (output
+// pixel, group of 8 channels) writes the group's 72 columns (c 9 + tap, 144 contiguous bytes)
+// as nine 16-byte stores; consecutive threads take consecutive groups, so a warp's stores are
+// contiguous, and each thread reads the 3 x 3 neighbourhoods of its 8 channels.
+__global__ void im2col_c8_kernel(const Im2colArgs a) {
+  const int cg_n = (a.cu + a.cs) / 8;
+  const int64_t P = (int64_t)a.batch * a.Ho * a.Wo;
+  const int H1 = a.up ? a.H / 2 : a.H, W1 = a.up ? a.W / 2 : a.W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * cg_n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int cg = (int)(t % cg_n);
+    const int64_t p = t / cg_n;
+    const int xo = (int)(p % a.Wo);
+    const int yo = (int)((p / a.Wo) % a.Ho);
+    const int b = (int)(p / ((int64_t)a.Wo * a.Ho));
+    __align__(16) __nv_bfloat16 v[72];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = cg * 8 + cc;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yi = a.stride * yo + tap / 3 - 1, xi = a.stride * xo + tap % 3 - 1;
+        float x = 0.f;
+        if (yi >= 0 && yi < a.H && xi >= 0 && xi < a.W) {
+          if (c < a.cu) {
+            const int ys = a.up ? yi >> 1 : yi, xs = a.up ? xi >> 1 : xi;
+            x = a.src1[((int64_t)c * a.batch + b) * H1 * W1 + (int64_t)ys * W1 + xs];
+          } else {
+            x = a.src2[((int64_t)(c - a.cu) * a.batch + b) * a.H * a.W + (int64_t)yi * a.W + xi];
+          }
+        }
+        v[cc * 9 + tap] = __float2bfloat16_rn(x);
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(a.cols + p * a.Kp + cg * 72);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dst[q] = reinterpret_cast<const uint4*>(v)[q];
+  }
+}
+
 // ---- input gradient as a convolution (stride-1 layers) --------------------------------------
 __global__ void im2col_bf16_kernel(const Im2colBf16Args a) {
   const int kg_n = a.Kp / 8;
@@ -113,6 +153,35 @@ __global__ void im2col_bf16_kernel(const Im2colBf16Args a) {
       v[j] = s;
     }
     *reinterpret_cast<uint4*>(a.cols + p * a.Kp + kg * 8) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// The same with 8 channels per thread (C a multiple of 8, Kp = 9 C).
+__global__ void im2col_bf16_c8_kernel(const Im2colBf16Args a) {
+  const int cg_n = a.C / 8;
+  const int64_t P = (int64_t)a.batch * a.H * a.W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * cg_n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int cg = (int)(t % cg_n);
+    const int64_t p = t / cg_n;
+    const int x = (int)(p % a.W);
+    const int y = (int)((p / a.W) % a.H);
+    const int b = (int)(p / ((int64_t)a.W * a.H));
+    __align__(16) __nv_bfloat16 v[72];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const __nv_bfloat16* s = a.src + ((int64_t)(cg * 8 + cc) * a.batch + b) * a.H * a.W;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yi = y + tap / 3 - 1, xi = x + tap % 3 - 1;
+        v[cc * 9 + tap] = (yi >= 0 && yi < a.H && xi >= 0 && xi < a.W)
+                              ? s[(int64_t)yi * a.W + xi]
+                              : __float2bfloat16_rn(0.f);
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(a.cols + p * a.Kp + cg * 72);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dst[q] = reinterpret_cast<const uint4*>(v)[q];
   }
 }
 
@@ -517,12 +586,23 @@ cudaError_t launch_uniform_fill(float* p, int64_t n, float scale, uint64_t seed,
 }
 
 cudaError_t launch_im2col(const Im2colArgs& a, cudaStream_t st) {
+  const int cin = a.cu + a.cs;
+  if (a.cu % 8 == 0 && cin % 8 == 0 && a.Kp == 9 * cin) {
+    const int64_t n = (int64_t)a.batch * a.Ho * a.Wo * (cin / 8);
+    im2col_c8_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const int64_t n = (int64_t)a.batch * a.Ho * a.Wo * (a.Kp / 8);
   im2col_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_im2col_bf16(const Im2colBf16Args& a, cudaStream_t st) {
+  if (a.C % 8 == 0 && a.Kp == 9 * a.C) {
+    const int64_t n = (int64_t)a.batch * a.H * a.W * (a.C / 8);
+    im2col_bf16_c8_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const int64_t n = (int64_t)a.batch * a.H * a.W * (a.Kp / 8);
   im2col_bf16_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a);
   return cudaGetLastError();
