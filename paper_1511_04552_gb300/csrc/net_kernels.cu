@@ -89,16 +89,16 @@ __global__ void im2col_kernel(const Im2colArgs a) {
 
 // Channel counts in multiples of 8 (every layer but the geometry input): one thread per (output
 // pixel, group of 8 channels) writes the group's 72 columns (c 9 + tap, 144 contiguous bytes)
-// as nine 16-byte stores; consecutive threads take consecutive groups, so a warp's stores are
-// contiguous, and each thread reads the 3 x 3 neighbourhoods of its 8 channels.
+// as nine 16-byte stores; consecutive threads take consecutive pixels of one group, so every
+// load of a warp reads consecutive pixels of one channel and tap.
 __global__ void im2col_c8_kernel(const Im2colArgs a) {
   const int cg_n = (a.cu + a.cs) / 8;
   const int64_t P = (int64_t)a.batch * a.Ho * a.Wo;
   const int H1 = a.up ? a.H / 2 : a.H, W1 = a.up ? a.W / 2 : a.W;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * cg_n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int cg = (int)(t % cg_n);
-    const int64_t p = t / cg_n;
+    const int64_t p = t % P;
+    const int cg = (int)(t / P);
     const int xo = (int)(p % a.Wo);
     const int yo = (int)((p / a.Wo) % a.Ho);
     const int b = (int)(p / ((int64_t)a.Wo * a.Ho));
@@ -162,8 +162,8 @@ __global__ void im2col_bf16_c8_kernel(const Im2colBf16Args a) {
   const int64_t P = (int64_t)a.batch * a.H * a.W;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * cg_n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int cg = (int)(t % cg_n);
-    const int64_t p = t / cg_n;
+    const int64_t p = t % P;
+    const int cg = (int)(t / P);
     const int x = (int)(p % a.W);
     const int y = (int)((p / a.W) % a.H);
     const int b = (int)(p / ((int64_t)a.W * a.H));
