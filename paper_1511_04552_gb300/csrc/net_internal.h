@@ -110,7 +110,7 @@ struct Col2imArgs {
 cudaError_t launch_col2im(const Col2imArgs& a, cudaStream_t st);
 
 // Backward of act(film(pre)) for one layer: dpre (BF16, [C][P]) and per (o, b) partial sums
-// {sum dpre, sum dz pre, sum dz} in FP64.
+// {sum dpre, sum dz pre, sum dz} (compensated FP32 per thread, FP64 across the block).
 struct ActBwdArgs {
   const float* dy;    // [C][P]
   const float* pre;   // [C][P]

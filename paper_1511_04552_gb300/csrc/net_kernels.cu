@@ -288,7 +288,14 @@ __global__ void act_backward_kernel(const ActBwdArgs a) {
     g = 1.f + f[o];
     beta = f[a.C + o];
   }
-  double acc[3] = {0.0, 0.0, 0.0};
+  // per-thread sums in FP32 with Neumaier compensation (FP64 arithmetic is a small fraction of
+  // GB300's FP32 rate), then the block sum in FP64; the order is fixed, so results repeat
+  float sum[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+  auto add = [&](int k, float x) {
+    const float t = sum[k] + x;
+    cmp[k] += fabsf(sum[k]) >= fabsf(x) ? (sum[k] - t) + x : (x - t) + sum[k];
+    sum[k] = t;
+  };
   const int64_t base = (int64_t)o * P + (int64_t)b * a.hw;
   for (int i = threadIdx.x; i < a.hw; i += blockDim.x) {
     const float pre = a.pre[base + i];
@@ -297,10 +304,13 @@ __global__ void act_backward_kernel(const ActBwdArgs a) {
     const float dz = a.act ? dy * dsilu_f(z) : dy;
     const float dpre = a.film ? dz * g : dz;
     a.dpre[base + i] = __float2bfloat16_rn(dpre);
-    acc[0] += (double)dpre;
-    acc[1] += (double)dz * (double)pre;
-    acc[2] += (double)dz;
+    add(0, dpre);
+    add(1, dz * pre);
+    add(2, dz);
   }
+  double acc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) acc[k] = (double)sum[k] + (double)cmp[k];
   block_sum<3>(acc, sh);
   if (threadIdx.x == 0) {
     double* out = a.partial + ((int64_t)o * a.batch + b) * 3;
@@ -423,15 +433,17 @@ __global__ void mlp_backward_w2_kernel(const MlpArgs a, const float* dr, float* 
 }
 
 // Backward, first layer: block j computes da1[b][j] = (sum_f W2[f][j] dr[b][f]) SiLU'(a1[b][j])
-// for every b (in f order), then gW1[j][i] = sum_b da1[b][j] c[b][i] and gb1[j] = sum_b da1[b][j]
-// (in batch order).
+// for every b (warp w < batch: its lanes take every 32nd f, then a fixed shuffle tree), then
+// gW1[j][i] = sum_b da1[b][j] c[b][i] and gb1[j] = sum_b da1[b][j] (in batch order).
 __global__ void mlp_backward_w1_kernel(const MlpArgs a, const float* dr, float* gW1, float* gb1) {
   extern __shared__ float da1[];  // [batch]
-  const int j = blockIdx.x;
-  for (int b = threadIdx.x; b < a.batch; b += blockDim.x) {
+  const int j = blockIdx.x, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int b = threadIdx.x >> 5; b < a.batch; b += nw) {
     float s = 0.f;
-    for (int f = 0; f < a.F; ++f) s += a.W2[(int64_t)f * a.H + j] * dr[(int64_t)b * a.F + f];
-    da1[b] = s * dsilu_f(a.a1[b * a.H + j]);
+    for (int f = lane; f < a.F; f += 32)
+      s += a.W2[(int64_t)f * a.H + j] * dr[(int64_t)b * a.F + f];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) da1[b] = s * dsilu_f(a.a1[b * a.H + j]);
   }
   __syncthreads();
   if (threadIdx.x < 4) {
@@ -673,7 +685,7 @@ cudaError_t launch_mlp_backward(const MlpArgs& a, const float* dr, float* gW1, f
                                                                                         gW2, gb2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  mlp_backward_w1_kernel<<<a.H, 32, sizeof(float) * (size_t)a.batch, st>>>(a, dr, gW1, gb1);
+  mlp_backward_w1_kernel<<<a.H, 512, sizeof(float) * (size_t)a.batch, st>>>(a, dr, gW1, gb1);
   return cudaGetLastError();
 }
 
