@@ -86,10 +86,16 @@ def test_stream_only_matches_oracle_pull():
         np.testing.assert_allclose(g[18:], r[18:], rtol=0, atol=2.5e-7)
 
 
-@pytest.mark.parametrize("w,pre", [(workloads.CAVITY_256, 3000), (workloads.CAVITY_1024, 200)])
+LARGE = dict(nx=4096, ny=2048, Ra=1e6, Pr=6.2, phi=0.02, d_p=50e-9)  # 8.4 M nodes, 1.8 GB
+
+
+@pytest.mark.parametrize("w,pre", [(workloads.CAVITY_256, 3000), (workloads.CAVITY_1024, 200),
+                                   (LARGE, 64)])
 def test_one_step_full_size(w, pre):
-    """At the benchmark sizes: evolve on the GPU (graph-captured launches, as timed), then one
-    more step on both sides from the identical exported state, compared plane by plane."""
+    """At the benchmark sizes (and a 4096 x 2048 lattice, 32 times the 1024^2 one, with two
+    nodes per thread over 32 768 tiles): evolve on the GPU (graph-captured launches, as timed),
+    then one more step on both sides from the identical exported state, compared plane by
+    plane."""
     import torch
     import oracle
     import paper_1511_04552_gb300 as m
