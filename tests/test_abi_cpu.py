@@ -105,6 +105,28 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
     assert L.mclbm_strerror(-5) == b"MCLBM_EDIVERGED"
 
 
+def test_steady_drivers_refuse_bad_arguments_without_device_work(pkg):
+    """mclbm_run_to_steady and mclbm_batch_run_to_steady check their arguments before any
+    device call; an unbound handle reports MCLBM_ESTATE from its first step."""
+    L = pkg.lib()
+    i64, dbl, cint = C.c_int64(), C.c_double(), C.c_int()
+    EINVAL, ESTATE = pkg.binding.EINVAL, pkg.binding.ESTATE
+    assert L.mclbm_run_to_steady(None, 1e-4, 1000, 10000, None, 0, C.byref(i64), C.byref(dbl),
+                                 C.byref(dbl), C.byref(cint)) == EINVAL
+    assert L.mclbm_batch_run_to_steady(None, 1e-4, 1000, 10000, None, 0, None, None,
+                                       C.byref(i64)) == EINVAL
+    h = pkg.create(16, 12, 1e3, 6.2, 0.01, 2e-8)
+    try:
+        for tol, every, lags, n_lags in ((0.0, 1000, None, 0), (1e-4, 0, None, 0),
+                                         (1e-4, 1000, (C.c_int32 * 1)(0), 1)):
+            assert L.mclbm_run_to_steady(h, tol, every, 10000, lags, n_lags, None, None, None,
+                                         None) == EINVAL
+        assert L.mclbm_run_to_steady(h, 1e-4, 1000, 10000, None, 0, None, None, None,
+                                     None) == ESTATE
+    finally:
+        L.mclbm_destroy(h)
+
+
 def test_storage_types_size_the_buffer(pkg):
     """16-bit storage halves the population planes of the bound buffer."""
     sizes = {}
