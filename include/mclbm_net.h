@@ -23,8 +23,11 @@
  *   then b[Cout], then W1[hidden][3], b1[hidden], W2[F][hidden], b2[F], F = 2(C4+C3+C2+C1+C0).
  * Every convolution is an im2col GEMM on the tensor cores with BF16 operands (activations,
  * weights, and in the backward pass the pre-activation gradient, each rounded to nearest) and
- * FP32 accumulation; everything else (FiLM, SiLU, the conditioning MLP, loss, reductions, Adam)
- * runs in FP32 CUDA-core kernels with FP64 sums.
+ * FP32 accumulation: the forward pass, the weight gradient, and the input gradient (for the
+ * stride-1 layers as the convolution of the pre-activation gradient with the flipped,
+ * transposed kernel; for the stride-2 layers as a GEMM into the column gradient and its
+ * fixed-order gather); everything else (FiLM, SiLU, the conditioning MLP, loss, reductions,
+ * Adam) runs in FP32 CUDA-core kernels with fixed-order sums (FP64 across blocks).
  *
  * Conventions: return MCLBM_OK (0) or a negative MCLBM_E* code (mclbm.h); the caller owns all
  * device memory (one workspace handed over by mclbm_net_bind, plus every input and output) and
@@ -107,10 +110,11 @@ int mclbm_net_train_step(mclbm_net_t* net, int batch, const float* cond_dev,
  *   D[z][m][n] = sum over k in split z of A(m, k) B(n, k),   0 <= m < M, 0 <= n < N,
  * A(m, k) = a[m*lda + k] (a_kmajor != 0) or a[k*lda + m]; B(n, k) likewise with b, ldb;
  * BF16 operands, FP32 result d[z*split_stride + m*ldd + n]; K is cut into `splits` ranges of
- * k_per_split (a multiple of 64), splits * k_per_split >= K. Operands are read with 16-byte
- * loads where the contiguous extent and the leading dimension are multiples of 8 elements and
- * the pointer is 16-byte aligned, element by element otherwise. EINVAL for non-positive sizes,
- * null or odd pointers, or a leading dimension below the contiguous extent. async. */
+ * k_per_split (a multiple of 64), splits * k_per_split >= K. When both operands have 16-byte
+ * aligned pointers and leading dimensions and contiguous extents in multiples of 8 elements,
+ * they are brought in by TMA tensor loads (128-byte swizzle) for a persistent, warp-specialised
+ * kernel; otherwise threads stage them (16-byte or element loads). EINVAL for non-positive
+ * sizes, null or odd pointers, or a leading dimension below the contiguous extent. async. */
 int mclbm_gemm_bf16(int M, int N, int K, const void* a, int64_t lda, int a_kmajor, const void* b,
                     int64_t ldb, int b_kmajor, float* d, int64_t ldd, int splits,
                     int64_t k_per_split, int64_t split_stride, void* cuda_stream);
