@@ -330,6 +330,18 @@ int mclbm_selftest_wait_timeout(void *cuda_stream, double *seconds);
 /* Time steps done since the last mclbm_init or mclbm_state_set (-1 for a NULL handle). */
 int64_t mclbm_steps_done(const mclbm_t *h);
 
+/* Which step kernel the handle launches, as chosen by mclbm_bind from the lattice size, the
+ * storage type, the device and the MCLBM_STEP_* environment overrides (no call in the paper: a
+ * diagnostic of this implementation). variant: 0 = the plain tile kernel (32 x 8 tiles, one CTA
+ * each), 2 = the TMA-staged persistent kernel; nodes_per_thread: 1 or 2; tile_h: the TMA
+ * kernel's tile height (8, or 7 where 32 x 8 tiles would give some SMs a second tile and 32 x 7
+ * tiles fit two per SM, e.g. 256 x 256 on 152 SMs; 8 for the tile kernel);
+ * grid: the TMA kernel's persistent CTAs (0 for the tile kernel); two: 1 when pairs of steps run
+ * in the two-step kernel. Outputs may be NULL. Host only, no GPU work. MCLBM_EINVAL for a NULL
+ * handle, MCLBM_ESTATE before mclbm_bind. */
+int mclbm_step_kernel(const mclbm_t *h, int *variant, int *nodes_per_thread, int *tile_h,
+                      int *grid, int *two);
+
 /* Text of the handle's latest error ("" if none); static text for a NULL handle. */
 const char *mclbm_last_error(const mclbm_t *h);
 

@@ -27,7 +27,7 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
            "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
            "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
            "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
-           "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc", "mclbm_save", "mclbm_load",
+           "mclbm_step_kernel", "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc", "mclbm_save", "mclbm_load",
            "mclbm_selftest_wait_timeout",
            "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
            "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
@@ -116,6 +116,9 @@ def lib():
         L.mclbm_load.restype = C.c_int
         L.mclbm_steps_done.argtypes = [vp]
         L.mclbm_steps_done.restype = C.c_int64
+        ip = C.POINTER(C.c_int)
+        L.mclbm_step_kernel.argtypes = [vp, ip, ip, ip, ip, ip]
+        L.mclbm_step_kernel.restype = C.c_int
         L.mclbm_last_error.argtypes = [vp]
         L.mclbm_last_error.restype = C.c_char_p
         L.mclbm_strerror.argtypes = [C.c_int]
@@ -270,6 +273,16 @@ class Cavity:
 
     def steps_done(self) -> int:
         return int(lib().mclbm_steps_done(self._h))
+
+    def step_kernel(self) -> dict:
+        """mclbm_step_kernel: the step kernel this cavity launches (variant, nodes per thread,
+        tile height, persistent CTAs, two-step pairs)."""
+        v = [C.c_int(0) for _ in range(5)]
+        rc = lib().mclbm_step_kernel(self._h, *[C.byref(x) for x in v])
+        if rc != 0:
+            raise MclbmError(rc, "mclbm_step_kernel")
+        return dict(zip(("variant", "nodes_per_thread", "tile_h", "grid", "two"),
+                        (x.value for x in v)))
 
     # -- the C entry points
     def init(self, mode=INIT_REST, warm=None):

@@ -284,7 +284,8 @@ int mclbm_bind(mclbm_t* h, void* dev_buf, size_t bytes, void* cuda_stream) {
   h->cfg.sr = h->props.rounding == MCLBM_ROUND_STOCHASTIC;
   if (h->cfg.variant == 2) {
     if (prepare_step(&h->cfg, h->L) != cudaSuccess ||
-        make_state_tensor_map(h->tmap, h->state[0], h->L, step_tile_width(h->cfg)) != cudaSuccess) {
+        make_state_tensor_map(h->tmap, h->state[0], h->L, step_tile_width(h->cfg), h->cfg.th) !=
+            cudaSuccess) {
       cudaGetLastError();
       h->cfg.variant = 0;
     }
@@ -615,6 +616,19 @@ int mclbm_get_consts(const mclbm_t* h, mclbm_consts* out) {
   return MCLBM_OK;
 }
 
+int mclbm_step_kernel(const mclbm_t* h, int* variant, int* nodes_per_thread, int* tile_h,
+                      int* grid, int* two) {
+  if (!h) return MCLBM_EINVAL;
+  if (!h->buf) return MCLBM_ESTATE;
+  const bool tma = h->cfg.variant == 2;
+  if (variant) *variant = h->cfg.variant;
+  if (nodes_per_thread) *nodes_per_thread = h->cfg.vec == 2 ? 2 : 1;
+  if (tile_h) *tile_h = tma ? h->cfg.th : 8;
+  if (grid) *grid = tma ? h->cfg.grid : 0;
+  if (two) *two = h->cfg.two ? 1 : 0;
+  return MCLBM_OK;
+}
+
 int64_t mclbm_steps_done(const mclbm_t* h) { return h ? h->steps : -1; }
 
 const char* mclbm_last_error(const mclbm_t* h) { return h ? h->err : "NULL handle"; }
@@ -804,7 +818,7 @@ int mclbm_batch_create(int n, mclbm_t* const* cavities, void* dev_buf, size_t by
     mclbm_t* h = cavities[c];
     std::memset(&host[c], 0, sizeof(BatchCav));
     CUtensorMap maps[2];
-    if (make_state_tensor_map(maps, h->state[0], h->L, kBatchTileW) != cudaSuccess)
+    if (make_state_tensor_map(maps, h->state[0], h->L, kBatchTileW, kBatchTileH) != cudaSuccess)
       return bail(MCLBM_ECUDA);
     host[c].map = maps[0];
     host[c].map_out = maps[1];

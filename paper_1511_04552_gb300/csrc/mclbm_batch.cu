@@ -16,7 +16,8 @@
 #include "mclbm_pair.cuh"
 
 namespace mcl {
-static_assert(pair::kTY == kTmaTY, "the tile table and the kernels share the tile height");
+static_assert(pair::kTY == kTmaTY && kBatchTileH == kTmaTY,
+              "the tile table, the tensor maps and the kernels share the tile height");
 
 // Tile table entry: cavity (10 bits) | tile column (11 bits) | tile row (11 bits).
 __host__ __device__ constexpr uint32_t pack_tile(int c, int tx, int ty) {
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(pair::Threads<2, kBatchTileW>::value,
                              tile_x(e) * kBatchTileW, tile_y(e) * pair::kTY, cv.L, cv.k,
                              cv.level[from ^ 1], sh ^ ((uint32_t)c << 24)};
   };
-  pair::tma_tile_loop<T, SR, ALLF, 2, kBatchTileW>(tile_of, n_tiles, err);
+  pair::tma_tile_loop<T, SR, ALLF, 2, kBatchTileW, pair::kTY>(tile_of, n_tiles, err);
 }
 
 // Nusselt sums of every cavity: block c reduces cavity c (the same sums as nusselt_kernel).

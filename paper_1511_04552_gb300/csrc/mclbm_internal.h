@@ -83,15 +83,17 @@ struct StepConfig {
   int vec;      // nodes per thread of the step kernels: 1 or 2 (0: chosen by lattice size)
   bool two;     // FP32: pairs of steps by the two-step kernel (set by prepare_two_f32)
   int grid2;    // two-step kernel: CTAs (one per 32 x 16 tile)
+  int th;       // TMA kernel: tile height, 8 or 7 (0 before prepare_step: chosen by lattice)
 };
 StepConfig choose_step_config(int nx, int ny, int np);
 // Device-dependent set-up of the chosen variant (shared-memory limit, persistent grid size);
 // may fall back to variant 0. Needs the device current.
 cudaError_t prepare_step(StepConfig* c, const Layout& L);
 // Tensor maps of the two-level state (x = column, y = row, z = plane of 54) for the TMA kernels
-// with tiles tile_w x 8: maps[0] loads input windows (the tile with 16 bytes of columns and 2
-// rows of halo on each side), maps[1] stores output tiles.
-cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w);
+// with tiles tile_w x tile_h: maps[0] loads input windows (the tile with 16 bytes of columns and
+// 2 rows of halo on each side), maps[1] stores output tiles.
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w,
+                                  int tile_h);
 // The two-step kernel's window loads (FP32): 32 x 16 tiles with 4 nodes of halo on each side.
 cudaError_t make_two_step_tensor_map(CUtensorMap* map, void* state0, const Layout& L);
 // Two-step kernel (FP32 storage): enables it in c when every SM can take one 32 x 16 tile
@@ -163,6 +165,7 @@ cudaError_t prepare_batch(int storage, int* per_sm);
 void build_tile_table(const std::vector<int>& nx, const std::vector<int>& ny,
                       const std::vector<int>& active, int order, std::vector<uint32_t>* out);
 constexpr int kBatchTileW = 64;  // batch tiles: 64 x 8 (two nodes per thread)
+constexpr int kBatchTileH = 8;
 int batch_size(const mclbm_batch_t* b);  // cavities of the batch (0 for NULL)
 
 }  // namespace mcl

@@ -311,6 +311,11 @@ StepConfig choose_step_config(int nx, int ny, int np) {
   // MCLBM_STEP_VEC = 1 | 2 forces the nodes per thread (comparisons; default by lattice size)
   const char* vv = std::getenv("MCLBM_STEP_VEC");
   c.vec = (vv && (vv[0] == '1' || vv[0] == '2') && vv[1] == 0) ? vv[0] - '0' : 0;
+  // MCLBM_STEP_TILE_H = 8 | 7 forces the TMA kernel's tile height with one node per thread
+  // (comparisons; default: 7 where 32 x 8 tiles would leave some SMs with a second tile and
+  // 32 x 7 tiles fit two per SM)
+  const char* th = std::getenv("MCLBM_STEP_TILE_H");
+  c.th = th && std::strcmp(th, "8") == 0 ? 8 : (th && std::strcmp(th, "7") == 0 ? 7 : 0);
   if (np != kPlanes) {  // two thermal sets: the plain tile kernel, one node per thread
     c.variant = 0;
     c.vec = 1;
@@ -349,7 +354,8 @@ cudaError_t launch_step(const StepArgs& a, const StepConfig& c, const CUtensorMa
 int step_tile_width(const StepConfig&) { return 32; }
 
 // maps[0]: window loads (box = window); maps[1]: output tile stores (box = tile).
-cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w) {
+cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout& L, int tile_w,
+                                  int tile_h) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -374,12 +380,12 @@ cudaError_t make_state_tensor_map(CUtensorMap* maps, void* state0, const Layout&
     default:
       return cudaErrorInvalidValue;
   }
-  if (tile_w != 32 && tile_w != 64) return cudaErrorInvalidValue;
+  if ((tile_w != 32 && tile_w != 64) || (tile_h != 8 && tile_h != 7)) return cudaErrorInvalidValue;
   const int wx = tile_w + 2 * (16 / L.elem);  // 16 bytes of halo columns on each side
   const cuuint64_t dims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)(2 * kPlanes)};
   const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * L.elem, (cuuint64_t)L.plane * L.elem};
-  const cuuint32_t box[3] = {(cuuint32_t)wx, (cuuint32_t)(kTmaTY + 4), (cuuint32_t)kPlanes};
-  const cuuint32_t tile[3] = {(cuuint32_t)tile_w, (cuuint32_t)kTmaTY, (cuuint32_t)kPlanes};
+  const cuuint32_t box[3] = {(cuuint32_t)wx, (cuuint32_t)(tile_h + 4), (cuuint32_t)kPlanes};
+  const cuuint32_t tile[3] = {(cuuint32_t)tile_w, (cuuint32_t)tile_h, (cuuint32_t)kPlanes};
   const cuuint32_t elem[3] = {1, 1, 1};
   CUresult r = encode(&maps[0], dt, 3, state0, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -295,24 +295,29 @@ __device__ __forceinline__ void pull(const Acc& acc, const Layout& L, int i, int
   }
 }
 
-// Shared-memory window of a TX x kTY tile (kTY = 8 rows): all 27 planes with XO columns (16
-// bytes: TMA's x alignment) and 2 rows of halo on each side.
-template <class T, int TX>
+constexpr int kTY = 8;     // tile height (single cavity and batch)
+constexpr int kLowTY = 7;  // low tiles: one node per thread, lattices of 1-2 tiles per SM
+
+// Shared-memory window of a TX x TY tile: all 27 planes with XO columns (16 bytes: TMA's x
+// alignment) and 2 rows of halo on each side. PADDED rounds its size up to 128 bytes, where an
+// output tile may follow.
+template <class T, int TX, int TY = kTY>
 struct PairWin {
   static constexpr int XO = 16 / (int)sizeof(T);
   static constexpr int WX = TX + 2 * XO;
-  static constexpr int WY = 8 + 4;
+  static constexpr int WY = TY + 4;
   static constexpr int WPLANE = WX * WY;
   static constexpr uint32_t BYTES = (uint32_t)kPlanes * WPLANE * sizeof(T);
-  static_assert(BYTES % 128 == 0, "windows stay 128-byte aligned");
+  static constexpr uint32_t PADDED = (BYTES + 127u) / 128u * 128u;
+  static_assert(BYTES % 16 == 0, "TMA transfers of 16-byte multiples");
 };
 
 // Accessor of a shared-memory window: element (wx, wy) of plane p at w[p * WPLANE + wy * WX + wx];
 // base = the position of node i (lane x).
-template <class T, int TX>
+template <class T, int TX, int TY = kTY>
 struct WinAcc {
   const T* base;
-  static constexpr int WX = PairWin<T, TX>::WX, WPLANE = PairWin<T, TX>::WPLANE;
+  static constexpr int WX = PairWin<T, TX, TY>::WX, WPLANE = PairWin<T, TX, TY>::WPLANE;
   __device__ __forceinline__ float a1(int p, int dx, int dy) const {
     return St<T>::ld1(base + p * WPLANE + dy * WX + dx);
   }
@@ -758,19 +763,21 @@ __device__ __forceinline__ void tile_collide(const StepConsts& k, const Layout& 
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-// Tiles of TX x kTY nodes with V nodes per thread: TX / V threads per tile row. The
+// Tiles of TX x TY nodes with V nodes per thread: TX / V threads per tile row. The
 // single-cavity kernels use 32-wide tiles (with two nodes per thread: four CTAs of 128 threads
 // per SM, which hide the window loads of each other better than two of 256); the batch uses 64.
-constexpr int kTY = 8;  // tile height
+// Tiles are 8 rows high, or 7 (one node per thread, 224 threads) on lattices where 32 x 8
+// tiles would put a second tile on some SMs and 32 x 7 tiles still fit two per SM.
 constexpr int kTileW = 32;  // single-cavity tile width
-template <int V, int TX>
+template <int V, int TX, int TY = kTY>
 struct Threads {
-  static constexpr int value = TX / V * kTY;
+  static constexpr int value = TX / V * TY;
 };
-// resident CTAs per SM the register budget is sized for (128 registers per thread)
-template <int V, int TX>
+// resident CTAs per SM the register budget is sized for (at least 128 registers per thread)
+template <int V, int TX, int TY = kTY>
 struct MinBlocks {
-  static constexpr int value = 65536 / 128 / Threads<V, TX>::value > 4 ? 4 : 65536 / 128 / Threads<V, TX>::value;
+  static constexpr int fit = 65536 / 128 / Threads<V, TX, TY>::value;
+  static constexpr int value = fit > 4 ? 4 : (fit < 1 ? 1 : fit);
 };
 
 // Plain tile kernel (small lattices): pulls from global memory (L1/L2), one tile per CTA.
@@ -803,15 +810,16 @@ __global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW
 // SM the kernel runs with, an output tile written back by one TMA store (16-bit storage; FP32
 // with one node per thread). FP32 with two nodes per thread (four CTAs per SM) stores each
 // pair straight to global memory.
-template <class T, int V, int TX_>
+template <class T, int V, int TX_, int TY_ = kTY>
 struct TmaPair {
-  static constexpr int TX = TX_;
-  static constexpr int XO = PairWin<T, TX>::XO;
-  static constexpr int WX = PairWin<T, TX>::WX;
-  static constexpr uint32_t BYTES = PairWin<T, TX>::BYTES;  // one input window
+  static constexpr int TX = TX_, TY = TY_;
+  static constexpr int XO = PairWin<T, TX, TY>::XO;
+  static constexpr int WX = PairWin<T, TX, TY>::WX;
+  static constexpr uint32_t BYTES = PairWin<T, TX, TY>::BYTES;  // one input window
+  static constexpr uint32_t OUT_AT = PairWin<T, TX, TY>::PADDED;  // the output tile's offset
   static constexpr bool STORE_TMA = sizeof(T) == 2 || V == 1;
-  static constexpr uint32_t OUT_BYTES = STORE_TMA ? (uint32_t)kPlanes * TX * kTY * sizeof(T) : 0;
-  static constexpr size_t SMEM = (size_t)BYTES + OUT_BYTES;
+  static constexpr uint32_t OUT_BYTES = STORE_TMA ? (uint32_t)kPlanes * TX * TY * sizeof(T) : 0;
+  static constexpr size_t SMEM = STORE_TMA ? (size_t)OUT_AT + OUT_BYTES : (size_t)BYTES;
 };
 
 struct TmaTileDesc {
@@ -831,23 +839,23 @@ struct TmaTileDesc {
 // load overlaps the collision; several CTAs per SM overlap each other. Every mbarrier wait is
 // bounded (2 s): on timeout the CTA sets bit 0 of the error word, drains its copies (bounded)
 // and returns. tile_of(tile) gives the tile's TmaTileDesc.
-template <class T, bool SR, bool ALLF, int V, int TX, class TileOf>
+template <class T, bool SR, bool ALLF, int V, int TX, int TY, class TileOf>
 __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles, int* err) {
-  using TP = TmaPair<T, V, TX>;
+  using TP = TmaPair<T, V, TX, TY>;
   constexpr int kTX = TX;
   constexpr uint32_t BYTES = TP::BYTES;
   constexpr bool STORE_TMA = TP::STORE_TMA;
   constexpr int XO = TP::XO;
   constexpr int WX = TP::WX;
   extern __shared__ __align__(128) unsigned char win_raw[];
-  __shared__ __align__(16) MomTile<kTX, kTY> mt;
+  __shared__ __align__(16) MomTile<kTX, TY> mt;
   __shared__ __align__(8) uint64_t bar_mem;
   __shared__ int s_abort;
   const int t = threadIdx.x;
   const uint32_t bar = tma::smem_u32(&bar_mem);
   const uint32_t win = tma::smem_u32(win_raw);
   const T* w = reinterpret_cast<const T*>(win_raw);
-  T* ob = reinterpret_cast<T*>(win_raw + BYTES);
+  T* ob = reinterpret_cast<T*>(win_raw + TP::OUT_AT);
   if (t == 0) {
     tma::mbar_init(bar, 1);
     tma::fence_barrier_init();
@@ -868,8 +876,10 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
     if (STORE_TMA && t == 0) tma::bulk_wait_read_0();
     vec<V> fw[kQ], fp[kQ], g[kQ];
     if (ok) {
-      auto acc_at = [&](int dx, int dy) { return WinAcc<T, kTX>{w + (2 + dy) * WX + (XO + dx)}; };
-      tile_pull<kTX, kTY, V, T, false>(acc_at, L, d.k, d.i0, d.j0, t, mt, fw, fp, g, nullptr);
+      auto acc_at = [&](int dx, int dy) {
+        return WinAcc<T, kTX, TY>{w + (2 + dy) * WX + (XO + dx)};
+      };
+      tile_pull<kTX, TY, V, T, false>(acc_at, L, d.k, d.i0, d.j0, t, mt, fw, fp, g, nullptr);
     } else {
       s_abort = 1;
     }
@@ -889,18 +899,18 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
       tma::mbar_expect_tx(bar, BYTES);
       tma::load_3d(win, dn.map, dn.i0 - XO, dn.j0 - 2, dn.z, bar);
     }
-    const TileThread<kTX, kTY, V> tt(t);
+    const TileThread<kTX, TY, V> tt(t);
     const int i = d.i0 + V * tt.c, j = d.j0 + tt.ty;
     const size_t o = (size_t)j * L.pitch + i;
     const uint32_t seed = SR ? mix32((uint32_t)o ^ d.hash) : 0u;
     if constexpr (STORE_TMA) {
-      TileSink<T, SR, kTX * kTY, V> out{ob + tt.ty * kTX + V * tt.c, seed};
-      tile_collide<ALLF, kTX, kTY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
+      TileSink<T, SR, kTX * TY, V> out{ob + tt.ty * kTX + V * tt.c, seed};
+      tile_collide<ALLF, kTX, TY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
                                                 out);
       tma::fence_proxy_async();  // generic-proxy writes of the output tile before the TMA store
     } else {
       GlobSink<T, SR, V> out{static_cast<T*>(d.dst) + o, L.plane, seed, i + 1 < L.nx};
-      tile_collide<ALLF, kTX, kTY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
+      tile_collide<ALLF, kTX, TY, V, T, false>(d.k, L, d.i0, d.j0, t, mt, fw, fp, g, nullptr,
                                                 out);
     }
     __syncthreads();  // the moment tile and the output tile are free again
@@ -913,8 +923,8 @@ __device__ __forceinline__ void tma_tile_loop(const TileOf& tile_of, int n_tiles
   if (STORE_TMA && t == 0) tma::bulk_wait_all();
 }
 
-template <class T, bool SR, bool ALLF, int V>
-__global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW>::value)
+template <class T, bool SR, bool ALLF, int V, int TY = kTY>
+__global__ void __launch_bounds__(Threads<V, kTileW, TY>::value, MinBlocks<V, kTileW, TY>::value)
     step_pair_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                          const __grid_constant__ CUtensorMap tmap_out, const StepArgs a) {
   // Programmatic dependent launch: let the next step's CTAs start their prologue while this
@@ -923,14 +933,14 @@ __global__ void __launch_bounds__(Threads<V, kTileW>::value, MinBlocks<V, kTileW
   asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int kTX = kTileW;
   const int tiles_x = (a.L.nx + kTX - 1) / kTX;
-  const int n_tiles = tiles_x * ((a.L.ny + kTY - 1) / kTY);
+  const int n_tiles = tiles_x * ((a.L.ny + TY - 1) / TY);
   const uint32_t sh = SR ? step_hash(a) : 0u;
   auto tile_of = [&](int tile) {
     const int ty = tile / tiles_x;
     return TmaTileDesc{&tmap, &tmap_out, a.z_src, kPlanes - a.z_src, (tile - ty * tiles_x) * kTX,
-                       ty * kTY, a.L, a.k, a.dst, sh};
+                       ty * TY, a.L, a.k, a.dst, sh};
   };
-  tma_tile_loop<T, SR, ALLF, V, kTileW>(tile_of, n_tiles, a.err);
+  tma_tile_loop<T, SR, ALLF, V, kTileW, TY>(tile_of, n_tiles, a.err);
 }
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -942,13 +952,23 @@ inline int nodes_per_thread(const Layout& L, int sms) {
   return tiles <= 2 * sms ? 1 : 2;
 }
 
-template <class T, int V>
+// Low tiles (32 x 7, one node per thread, two CTAs per SM) when 32 x 8 tiles would put a
+// second tile on some SMs and 32 x 7 tiles fit two per SM: the busiest SMs then compute 448
+// nodes instead of 512 (measured on the 256 x 256 lattice: 4.65 us per step against 4.87; one
+// CTA of 32 x 14 per SM, the same 448 nodes, takes 5.21 us: two CTAs overlap each other's
+// barriers and window loads).
+inline bool low_tiles_pay(const Layout& L, int sms) {
+  const int tx = (L.nx + kTileW - 1) / kTileW;
+  return tx * ((L.ny + kTY - 1) / kTY) > sms && tx * ((L.ny + kLowTY - 1) / kLowTY) <= 2 * sms;
+}
+
+template <class T, int V, int TY>
 cudaError_t prepare_pair_tma_v(StepConfig* c, const Layout& L, int sms) {
-  const size_t smem = TmaPair<T, V, kTileW>::SMEM;
-  const void* fns[4] = {(const void*)step_pair_tma_kernel<T, false, false, V>,
-                        (const void*)step_pair_tma_kernel<T, false, true, V>,
-                        (const void*)step_pair_tma_kernel<T, true, false, V>,
-                        (const void*)step_pair_tma_kernel<T, true, true, V>};
+  const size_t smem = TmaPair<T, V, kTileW, TY>::SMEM;
+  const void* fns[4] = {(const void*)step_pair_tma_kernel<T, false, false, V, TY>,
+                        (const void*)step_pair_tma_kernel<T, false, true, V, TY>,
+                        (const void*)step_pair_tma_kernel<T, true, false, V, TY>,
+                        (const void*)step_pair_tma_kernel<T, true, true, V, TY>};
   cudaError_t e;
   for (const void* fn : fns)
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -956,14 +976,15 @@ cudaError_t prepare_pair_tma_v(StepConfig* c, const Layout& L, int sms) {
       return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, step_pair_tma_kernel<T, true, true, V>, Threads<V, kTileW>::value, smem);
+      &per_sm, step_pair_tma_kernel<T, true, true, V, TY>, Threads<V, kTileW, TY>::value, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (per_sm > MinBlocks<V, kTileW>::value) per_sm = MinBlocks<V, kTileW>::value;
+  if (per_sm > MinBlocks<V, kTileW, TY>::value) per_sm = MinBlocks<V, kTileW, TY>::value;
   constexpr int kTX = kTileW;
-  const int tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
+  const int tiles = ((L.nx + kTX - 1) / kTX) * ((L.ny + TY - 1) / TY);
   c->grid = tiles < per_sm * sms ? tiles : per_sm * sms;
   c->vec = V;
+  c->th = TY;
   return cudaSuccess;
 }
 
@@ -976,7 +997,11 @@ cudaError_t prepare_pair_tma_t(StepConfig* c, const Layout& L) {
     return e;
   int v = nodes_per_thread(L, sms);
   if (c->vec == 1 || c->vec == 2) v = c->vec;  // forced by the caller
-  return v == 1 ? prepare_pair_tma_v<T, 1>(c, L, sms) : prepare_pair_tma_v<T, 2>(c, L, sms);
+  if (v == 2) return prepare_pair_tma_v<T, 2, kTY>(c, L, sms);
+  // tile height: forced by the caller (8 or 7), else 7 where low tiles pay
+  const bool low = c->th == kLowTY || (c->th != kTY && low_tiles_pay(L, sms));
+  return low ? prepare_pair_tma_v<T, 1, kLowTY>(c, L, sms)
+             : prepare_pair_tma_v<T, 1, kTY>(c, L, sms);
 }
 
 template <class T, bool SR, bool ALLF, int V>
@@ -993,6 +1018,15 @@ cudaError_t launch_pair_t4(const StepArgs& a, const StepConfig& c, const CUtenso
   if (c.variant == 2) {
     if (!map || c.grid < 1) return cudaErrorInvalidValue;
     cfg.gridDim = dim3(c.grid);
+    if constexpr (V == 1) {
+      if (c.th == kLowTY) {
+        cfg.blockDim = dim3(Threads<1, kTileW, kLowTY>::value);
+        cfg.dynamicSmemBytes = TmaPair<T, 1, kTileW, kLowTY>::SMEM;
+        return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<T, SR, ALLF, 1, kLowTY>, map[0],
+                                  map[1], a);
+      }
+    }
+    if (c.th != kTY) return cudaErrorInvalidValue;
     cfg.blockDim = dim3(Threads<V, kTileW>::value);
     cfg.dynamicSmemBytes = TmaPair<T, V, kTileW>::SMEM;
     return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<T, SR, ALLF, V>, map[0], map[1], a);

@@ -93,6 +93,9 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
         assert L.mclbm_nusselt(h, C.byref(a), C.byref(b)) == pkg.binding.ESTATE
         assert b"mclbm_bind" in L.mclbm_last_error(h)
         assert L.mclbm_steps_done(h) == 0
+        v = C.c_int(-7)
+        assert L.mclbm_step_kernel(h, C.byref(v), None, None, None, None) == pkg.binding.ESTATE
+        assert v.value == -7
         n = L.mclbm_buffer_bytes(h)
         assert n >= 2 * 27 * 32 * 12 * 4 + 12 * 16 * 4 * 12
         assert L.mclbm_bind(h, None, n, None) == pkg.binding.EINVAL
@@ -100,6 +103,7 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
     finally:
         L.mclbm_destroy(h)
     assert L.mclbm_steps_done(None) == -1
+    assert L.mclbm_step_kernel(None, None, None, None, None, None) == pkg.binding.EINVAL
     assert L.mclbm_last_error(None) == b"NULL handle"
     L.mclbm_destroy(None)
     assert L.mclbm_strerror(-5) == b"MCLBM_EDIVERGED"

@@ -287,6 +287,66 @@ def test_two_step_kernel_equals_single_steps(nx, ny, mask, steps, monkeypatch):
     assert two.nusselt() == one.nusselt()
 
 
+@pytest.mark.parametrize("nx,ny,storage,rounding", [
+    (64, 32, 0, 1),     # 32 rows: tile rows of 7, 7, 7, 7 and 4
+    (130, 35, 0, 1),    # ragged tiles in x; 35 = 5 x 7
+    (200, 67, 1, 1),    # FP16, round to nearest
+    (200, 67, 1, 0),    # FP16, stochastic rounding (per-node streams do not depend on tiles)
+    (96, 90, 2, 0),     # BF16
+])
+def test_tile_heights_bitwise_identical(nx, ny, storage, rounding, monkeypatch):
+    """The TMA kernel with 32 x 7 tiles and with 32 x 8 tiles (one node per thread) gives the
+    same states bit for bit after 300 steps: the tile height changes which CTA computes a node,
+    not its arithmetic. The handle reports the kernel it launches."""
+    import torch
+    import paper_1511_04552_gb300 as m
+    monkeypatch.setenv("MCLBM_STEP_VARIANT", "tma")
+    monkeypatch.setenv("MCLBM_STEP_VEC", "1")
+    states, nus = {}, {}
+    for th in ("7", "8"):
+        monkeypatch.setenv("MCLBM_STEP_TILE_H", th)
+        cav = m.Cavity(nx, ny, 1e5, 6.2, 0.03, 30e-9, storage=storage, rounding=rounding).init()
+        k = cav.step_kernel()
+        assert (k["variant"], k["nodes_per_thread"], k["tile_h"]) == (2, 1, int(th)), k
+        tiles = -(-nx // 32) * -(-ny // int(th))
+        assert 1 <= k["grid"] <= tiles
+        cav.step(300)
+        states[th] = cav.state_get()
+        nus[th] = cav.nusselt()
+    assert torch.equal(states["7"], states["8"])
+    assert nus["7"] == nus["8"]
+
+
+def test_benchmark_lattice_uses_low_tiles():
+    """On the 256 x 256 benchmark lattice 32 x 8 tiles (256) would put a second tile on 104 of
+    the 152 SMs; 32 x 7 tiles (8 x 37 = 296) fit two per SM, so the handle picks them (the
+    busiest SMs compute 448 nodes instead of 512), and one step from an evolved state still
+    equals the oracle's."""
+    import paper_1511_04552_gb300 as m
+    import torch
+    import oracle
+    w = workloads.CAVITY_256
+    gpu = m.Cavity(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"]).init()
+    k = gpu.step_kernel()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if not (256 > sms and 296 <= 2 * sms):
+        pytest.skip("the low-tile rule applies for 148 to 255 SMs")
+    assert (k["variant"], k["nodes_per_thread"], k["tile_h"], k["grid"]) == (2, 1, 7, 296), k
+    gpu.step(500)
+    st_abs = P.gpu_state_abs(gpu)
+    gpu.step(1)
+    after = P.gpu_state_abs(gpu)
+    ref = oracle.RefSolver(w["nx"], w["ny"], w["Ra"], w["Pr"], w["phi"], w["d_p"])
+    ref.set_state(st_abs)
+    ref.step(1)
+    c = gpu.consts()
+    dev_ref = P.abs_to_dev(ref.get_state(), c)
+    dev_gpu = P.abs_to_dev(after, c)
+    for q in range(27):
+        e = P.rel_l2(dev_gpu[q], dev_ref[q])
+        assert e < 1e-5, (q, e)
+
+
 def test_warm_init_with_density_matches_oracle():
     """MCLBM_INIT_WARM_RHO (ux, uy, theta, phi, rho^w) against the oracle's same init, then 500
     steps."""
