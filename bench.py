@@ -397,9 +397,7 @@ def main():
         cav.step(CH)
         if ev is not None:
             ev[1].record(st)
-        cav.nusselt()
-        cav.residual()
-        cav.mass()
+        cav.diagnostics()  # Nu, masses and residual: one synchronisation
         flush.zero_()
 
     for _ in range(args.warmup):

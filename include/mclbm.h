@@ -159,7 +159,10 @@ int mclbm_bind(mclbm_t *h, void *dev_buf, size_t bytes, void *cuda_stream);
 int mclbm_init(mclbm_t *h, int mode, const float *warm_dev);
 
 /* Advances n >= 0 time steps (Eqs 18-19 with the forces of Table 1 and the walls of
- * Eqs 34-36), in captured CUDA graphs of 64 steps plus single launches. Async. A step kernel
+ * Eqs 34-36): the even part in captured CUDA graphs of 2^k steps (2 <= 2^k <= 1024, largest
+ * first, built on first use and kept with the handle), an odd last step as a single launch; the
+ * stochastic-rounding streams of 16-bit storage follow the graphs' replay count, so a given
+ * sequence of calls is reproducible bit for bit. Async. A step kernel
  * that gives up a bounded wait on its own data movement sets an error word instead of
  * hanging; the next mclbm_nusselt, mclbm_mass or mclbm_residual returns MCLBM_ETIMEOUT. */
 int mclbm_step(mclbm_t *h, int64_t n);
@@ -186,6 +189,14 @@ int mclbm_mass(mclbm_t *h, double *mass_w, double *mass_p);
  * r = max over q in {u, theta, phi} of ||q_now - q_then||_2 / (K ||q_now||_2) (0 when K = 0),
  * FP64 sums. Replaces the snapshot. Syncs. MCLBM_EDIVERGED if non-finite. */
 int mclbm_residual(mclbm_t *h, double *r);
+
+/* The three reductions above in one call with one host synchronisation (Sec. 2.d's Nu at the
+ * walls, Eq 29's masses, the residual): the same FP64 sums and results as mclbm_nusselt,
+ * mclbm_mass and mclbm_residual called in that order (the residual's snapshot is replaced).
+ * Syncs once. MCLBM_EINVAL for a NULL output; MCLBM_EDIVERGED if any result is non-finite (every
+ * output is still written); MCLBM_ETIMEOUT as the single calls. */
+int mclbm_diagnostics(mclbm_t *h, double *nu_hot, double *nu_cold, double *mass_w,
+                      double *mass_p, double *r);
 
 /* Copies the population planes [np][ny][nx] FP32 (np = 27: f^w_0..8, f^p_0..8, g_0..8; with
  * two thermal sets np = 36: f^w, f^p, g^w, g^p; directions in the order of Eq 21: rest, +x, +y,

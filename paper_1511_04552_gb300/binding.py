@@ -20,15 +20,14 @@ THETA_W, THETA_P = 256, 512  # the thermal sets' own temperatures (= THETA with 
 INIT_REST, INIT_WARM, INIT_WARM_RHO = 0, 2, 3
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
-GRAPH_STEPS = 64
 
 # every entry point declared in include/mclbm.h
 EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer_bytes",
            "mclbm_bind", "mclbm_init", "mclbm_step", "mclbm_stream_only", "mclbm_fields",
-           "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_state_get",
-           "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts", "mclbm_steps_done",
-           "mclbm_step_kernel", "mclbm_last_error", "mclbm_strerror", "mclbm_mass_noalloc", "mclbm_save", "mclbm_load",
-           "mclbm_selftest_wait_timeout",
+           "mclbm_nusselt", "mclbm_mass", "mclbm_residual", "mclbm_diagnostics",
+           "mclbm_state_get", "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts",
+           "mclbm_steps_done", "mclbm_step_kernel", "mclbm_last_error", "mclbm_strerror",
+           "mclbm_mass_noalloc", "mclbm_save", "mclbm_load", "mclbm_selftest_wait_timeout",
            "mclbm_batch_buffer_bytes", "mclbm_batch_create", "mclbm_batch_step",
            "mclbm_batch_nusselt", "mclbm_batch_set_active", "mclbm_batch_tune",
            "mclbm_batch_last_error", "mclbm_batch_destroy",
@@ -104,6 +103,7 @@ def lib():
         L.mclbm_nusselt.argtypes = [vp, dp, dp]
         L.mclbm_mass.argtypes = [vp, dp, dp]
         L.mclbm_residual.argtypes = [vp, dp]
+        L.mclbm_diagnostics.argtypes = [vp, dp, dp, dp, dp, dp]
         L.mclbm_state_get.argtypes = [vp, vp]
         L.mclbm_state_set.argtypes = [vp, vp]
         L.mclbm_run_host.argtypes = [vp, fp, C.c_int64, C.c_uint32, fp, dp, dp]
@@ -180,8 +180,8 @@ def lib():
             getattr(L, name).restype = C.c_int
         for name in ("mclbm_create", "mclbm_bind", "mclbm_init", "mclbm_step",
                      "mclbm_stream_only", "mclbm_fields", "mclbm_nusselt", "mclbm_mass",
-                     "mclbm_residual", "mclbm_state_get", "mclbm_state_set", "mclbm_run_host",
-                     "mclbm_get_consts"):
+                     "mclbm_residual", "mclbm_diagnostics", "mclbm_state_get",
+                     "mclbm_state_set", "mclbm_run_host", "mclbm_get_consts"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -341,6 +341,14 @@ class Cavity:
         r = C.c_double()
         self._check(lib().mclbm_residual(self._h, C.byref(r)), "mclbm_residual")
         return r.value
+
+    def diagnostics(self) -> dict:
+        """mclbm_diagnostics: Nusselt numbers, masses and residual with one synchronisation."""
+        v = [C.c_double() for _ in range(5)]
+        self._check(lib().mclbm_diagnostics(self._h, *[C.byref(x) for x in v]),
+                    "mclbm_diagnostics")
+        return dict(zip(("nu_hot", "nu_cold", "mass_w", "mass_p", "residual"),
+                        (x.value for x in v)))
 
     def state_get(self, out=None):
         if out is None:

@@ -41,9 +41,9 @@ struct mclbm {
   bool initialised = false;
   bool diverged = false;
   int64_t steps = 0, snap_steps = 0;
-  // graphs of kGraphSteps steps starting from time level 0 or 1
+  // graph[from][k]: 2^k steps starting from time level 0 or 1 (built on first use)
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2][kGraphLogMax + 1] = {};
   char err[512] = {0};
 };
 
@@ -88,7 +88,7 @@ Regions regions(const mclbm_t* h) {
   r.partials = off;
   off += align_up((size_t)kMaxRedBlocks * kRedWidth * sizeof(double), 256);
   r.red = off;
-  off += align_up((size_t)kRedWidth * sizeof(double), 256);
+  off += align_up((size_t)3 * kRedWidth * sizeof(double), 256);  // mclbm_diagnostics: 3 slots
   r.err = off;
   off += 256;
   r.total = off;
@@ -108,10 +108,11 @@ int ready(mclbm_t* h, bool need_init) {
 
 void drop_graphs(mclbm_t* h) {
   for (int p = 0; p < 2; ++p)
-    if (h->graph[p]) {
-      cudaGraphExecDestroy(h->graph[p]);
-      h->graph[p] = nullptr;
-    }
+    for (int k = 0; k <= kGraphLogMax; ++k)
+      if (h->graph[p][k]) {
+        cudaGraphExecDestroy(h->graph[p][k]);
+        h->graph[p][k] = nullptr;
+      }
 }
 
 StepArgs step_args(const mclbm_t* h, int from, uint32_t seed) {
@@ -127,18 +128,19 @@ StepArgs step_args(const mclbm_t* h, int from, uint32_t seed) {
   return a;
 }
 
-// Captures kGraphSteps alternating launches starting from time level `from`.
-int build_graph(mclbm_t* h, int from) {
+// Captures 2^k (k >= 1) alternating step launches starting from time level `from`.
+int build_graph(mclbm_t* h, int from, int k) {
   if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const int n = 1 << k;
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
-  if (h->cfg.two) {  // pairs of steps: kGraphSteps / 2 launches, the level alternating per pair
-    for (int s = 0; s < kGraphSteps / 2 && le == cudaSuccess; ++s)
+  if (h->cfg.two) {  // pairs of steps: n / 2 launches, the level alternating per pair
+    for (int s = 0; s < n / 2 && le == cudaSuccess; ++s)
       le = launch_two_f32(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, &h->tmap2,
                           h->cap_stream);
   } else {
-    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s)
+    for (int s = 0; s < n && le == cudaSuccess; ++s)
       le = launch_step(step_args(h, (from + s) & 1, (uint32_t)s), h->cfg, h->tmap,
                        h->cap_stream);
   }
@@ -150,10 +152,10 @@ int build_graph(mclbm_t* h, int from) {
     return cuda_fail(h, le, "launch_step (capture)");
   }
   if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
-  cudaError_t ie = cudaGraphInstantiate(&h->graph[from], g, 0);
+  cudaError_t ie = cudaGraphInstantiate(&h->graph[from][k], g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) {
-    h->graph[from] = nullptr;
+    h->graph[from][k] = nullptr;
     return cuda_fail(h, ie, "cudaGraphInstantiate");
   }
   return MCLBM_OK;
@@ -334,21 +336,22 @@ int mclbm_step(mclbm_t* h, int64_t n) {
   int rc = ready(h, true);
   if (rc) return rc;
   if (n < 0) return fail(h, MCLBM_EINVAL, "negative step count");
+  // the even part in graphs of 2^k steps, largest first (1000 = 512 + 256 + 128 + 64 + 32 + 8;
+  // each graph boundary costs about 4 us of idle GPU), an odd last step as a single launch
   int64_t left = n;
-  while (left >= kGraphSteps) {
-    if (!h->graph[h->cur]) {
-      rc = build_graph(h, h->cur);
+  while (left >= 2) {
+    int k = 1;
+    while (k < kGraphLogMax && (int64_t(2) << k) <= left) ++k;
+    if (!h->graph[h->cur][k]) {
+      rc = build_graph(h, h->cur, k);
       if (rc) return rc;
     }
-    CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-    left -= kGraphSteps;  // even: the current time level is unchanged
-    h->steps += kGraphSteps;
-  }
-  for (; h->cfg.two && left >= 2; left -= 2) {  // a pair of steps moves to the other level
-    CK(h, launch_two_f32(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg,
-                         &h->tmap2, h->stream));
-    h->cur ^= 1;
-    h->steps += 2;
+    CK(h, cudaGraphLaunch(h->graph[h->cur][k], h->stream));
+    left -= int64_t(1) << k;
+    h->steps += int64_t(1) << k;
+    // an even number of single steps ends on the level it started from; a pair of steps of
+    // the two-step kernel moves to the other level, so 2^(k-1) pairs do so only for k = 1
+    if (h->cfg.two && k == 1) h->cur ^= 1;
   }
   for (; left > 0; --left) {
     CK(h, launch_step(step_args(h, h->cur, 0x80000000u ^ (uint32_t)h->steps), h->cfg, h->tmap,
@@ -376,6 +379,54 @@ int mclbm_fields(mclbm_t* h, uint32_t which, float* dev_out) {
   return MCLBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Host halves of the reductions: from the FP64 sums on the device to the reported numbers.
+int nusselt_from(mclbm_t* h, const double* s, double* nu_hot, double* nu_cold) {
+  const double scale = h->c.k_ratio * (double)h->nx / (double)h->ny;  // L / dT, dT = 1
+  *nu_hot = s[0] * scale;
+  *nu_cold = s[1] * scale;
+  if (!std::isfinite(*nu_hot) || !std::isfinite(*nu_cold)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite Nusselt number");
+  return MCLBM_OK;
+}
+
+int mass_from(mclbm_t* h, const double* s, double* mass_w, double* mass_p) {
+  const double n = (double)h->nx * h->ny;
+  *mass_w = s[0] + n * h->c.rho_w0;
+  *mass_p = s[1] + n * h->c.rho_p0;
+  if (!std::isfinite(*mass_w) || !std::isfinite(*mass_p)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite mass");
+  return MCLBM_OK;
+}
+
+// K steps since the snapshot; s = the six sums (||q_now - q_then||^2, ||q_now||^2 for u,
+// theta, phi), unused when K = 0.
+int residual_from(mclbm_t* h, int64_t K, const double* s, double* r) {
+  double res = 0.0;
+  for (int g = 0; K > 0 && g < 3; ++g) {
+    const double num = s[2 * g], den = s[2 * g + 1];
+    double term;
+    if (num == 0.0)
+      term = 0.0;
+    else if (den == 0.0)
+      term = INFINITY;
+    else
+      term = std::sqrt(num) / ((double)K * std::sqrt(den));
+    if (term > res || std::isnan(term)) res = term;
+  }
+  *r = res;
+  if (std::isnan(res)) h->diverged = true;
+  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite residual");
+  return MCLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mclbm_nusselt(mclbm_t* h, double* nu_hot, double* nu_cold) {
   int rc = ready(h, true);
   if (rc) return rc;
@@ -384,12 +435,7 @@ int mclbm_nusselt(mclbm_t* h, double* nu_hot, double* nu_cold) {
   double s[2];
   rc = d2h_sync(h, s, h->red, sizeof(s));
   if (rc) return rc;
-  const double scale = h->c.k_ratio * (double)h->nx / (double)h->ny;  // L / dT, dT = 1
-  *nu_hot = s[0] * scale;
-  *nu_cold = s[1] * scale;
-  if (!std::isfinite(*nu_hot) || !std::isfinite(*nu_cold)) h->diverged = true;
-  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite Nusselt number");
-  return MCLBM_OK;
+  return nusselt_from(h, s, nu_hot, nu_cold);
 }
 
 int mclbm_mass(mclbm_t* h, double* mass_w, double* mass_p) {
@@ -400,12 +446,7 @@ int mclbm_mass(mclbm_t* h, double* mass_w, double* mass_p) {
   double s[2];
   rc = d2h_sync(h, s, h->red, sizeof(s));
   if (rc) return rc;
-  const double n = (double)h->nx * h->ny;
-  *mass_w = s[0] + n * h->c.rho_w0;
-  *mass_p = s[1] + n * h->c.rho_p0;
-  if (!std::isfinite(*mass_w) || !std::isfinite(*mass_p)) h->diverged = true;
-  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite mass");
-  return MCLBM_OK;
+  return mass_from(h, s, mass_w, mass_p);
 }
 
 int mclbm_residual(mclbm_t* h, double* r) {
@@ -416,29 +457,37 @@ int mclbm_residual(mclbm_t* h, double* r) {
   CK(h, launch_residual(h->state[h->cur], h->L, h->k, h->snap, K > 0, h->partials, h->red,
                         h->stream));
   h->snap_steps = h->steps;
-  double res = 0.0;
+  double s[6] = {0, 0, 0, 0, 0, 0};
   if (K > 0) {
-    double s[6];
     rc = d2h_sync(h, s, h->red, sizeof(s));
     if (rc) return rc;
-    for (int g = 0; g < 3; ++g) {
-      const double num = s[2 * g], den = s[2 * g + 1];
-      double term;
-      if (num == 0.0)
-        term = 0.0;
-      else if (den == 0.0)
-        term = INFINITY;
-      else
-        term = std::sqrt(num) / ((double)K * std::sqrt(den));
-      if (term > res || std::isnan(term)) res = term;
-    }
   } else {
     CK(h, cudaStreamSynchronize(h->stream));
   }
-  *r = res;
-  if (std::isnan(res)) h->diverged = true;
-  if (h->diverged) return fail(h, MCLBM_EDIVERGED, "non-finite residual");
-  return MCLBM_OK;
+  return residual_from(h, K, s, r);
+}
+
+int mclbm_diagnostics(mclbm_t* h, double* nu_hot, double* nu_cold, double* mass_w,
+                      double* mass_p, double* r) {
+  int rc = ready(h, true);
+  if (rc) return rc;
+  if (!nu_hot || !nu_cold || !mass_w || !mass_p || !r)
+    return fail(h, MCLBM_EINVAL, "NULL output");
+  // the three reductions one after another on the stream, each into its own slot of the
+  // result area (the partial sums are reused in stream order), then one copy and one wait
+  const int64_t K = h->steps - h->snap_steps;
+  CK(h, launch_nusselt(h->state[h->cur], h->L, h->k, h->red, h->stream));
+  CK(h, launch_mass(h->state[h->cur], h->L, h->partials, h->red + kRedWidth, h->stream));
+  CK(h, launch_residual(h->state[h->cur], h->L, h->k, h->snap, K > 0, h->partials,
+                        h->red + 2 * kRedWidth, h->stream));
+  h->snap_steps = h->steps;
+  double s[3 * kRedWidth];
+  rc = d2h_sync(h, s, h->red, sizeof(s));
+  if (rc) return rc;
+  const int r1 = nusselt_from(h, s, nu_hot, nu_cold);
+  const int r2 = mass_from(h, s + kRedWidth, mass_w, mass_p);
+  const int r3 = residual_from(h, K, s + 2 * kRedWidth, r);
+  return r1 ? r1 : (r2 ? r2 : r3);
 }
 
 int mclbm_state_get(mclbm_t* h, float* dev_out) {

@@ -17,7 +17,8 @@ constexpr int kPlanes = 27;  // f^w, f^p, g (one thermal set)
 constexpr int kPlanes2 = 36; // f^w, f^p, g^w, g^p (two thermal sets)
 constexpr int kFields = 10;  // MCLBM_UX ... MCLBM_THETA_P
 constexpr uint32_t kFieldMask = (1u << kFields) - 1u;
-constexpr int kGraphSteps = 64;     // steps per captured graph (even: the buffers come back)
+constexpr int kGraphSteps = 64;     // steps per captured batch graph (even: the buffers come back)
+constexpr int kGraphLogMax = 10;    // single cavity: graphs of 2^k steps, k = 1 .. kGraphLogMax
 constexpr int kMaxRedBlocks = 304;  // reduction partials: 2 CTAs per SM on 152 SMs
 constexpr int kRedWidth = 8;        // doubles per reduction partial
 

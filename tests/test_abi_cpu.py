@@ -93,6 +93,8 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
         assert L.mclbm_nusselt(h, C.byref(a), C.byref(b)) == pkg.binding.ESTATE
         assert b"mclbm_bind" in L.mclbm_last_error(h)
         assert L.mclbm_steps_done(h) == 0
+        d = [C.c_double() for _ in range(5)]
+        assert L.mclbm_diagnostics(h, *[C.byref(x) for x in d]) == pkg.binding.ESTATE
         v = C.c_int(-7)
         assert L.mclbm_step_kernel(h, C.byref(v), None, None, None, None) == pkg.binding.ESTATE
         assert v.value == -7
@@ -104,6 +106,7 @@ def test_unbound_handle_is_refused_without_device_work(pkg):
         L.mclbm_destroy(h)
     assert L.mclbm_steps_done(None) == -1
     assert L.mclbm_step_kernel(None, None, None, None, None, None) == pkg.binding.EINVAL
+    assert L.mclbm_diagnostics(None, None, None, None, None, None) == pkg.binding.EINVAL
     assert L.mclbm_last_error(None) == b"NULL handle"
     L.mclbm_destroy(None)
     assert L.mclbm_strerror(-5) == b"MCLBM_EDIVERGED"

@@ -155,6 +155,24 @@ def test_residual_matches_oracle():
     assert gpu.residual() == 0.0  # no steps since the last check
 
 
+def test_diagnostics_equal_the_single_reductions():
+    """mclbm_diagnostics (three reductions, one synchronisation) returns exactly what
+    mclbm_nusselt, mclbm_mass and mclbm_residual return on an identical cavity, including the
+    residual's snapshot handling (0 right after a call)."""
+    import paper_1511_04552_gb300 as m
+    a = m.Cavity(70, 45, 1e5, 6.2, 0.03, 30e-9).init()
+    b = m.Cavity(70, 45, 1e5, 6.2, 0.03, 30e-9).init()
+    for n in (500, 333):
+        a.step(n)
+        b.step(n)
+        nu, ms, r = a.nusselt(), a.mass(), a.residual()
+        d = b.diagnostics()
+        assert (d["nu_hot"], d["nu_cold"]) == nu
+        assert (d["mass_w"], d["mass_p"]) == ms
+        assert d["residual"] == r and r > 0
+    assert b.diagnostics()["residual"] == 0.0 == a.residual()
+
+
 def test_graph_and_single_launches_agree_bitwise():
     import torch
     import paper_1511_04552_gb300 as m
@@ -261,7 +279,7 @@ def test_step_variants_bitwise_identical(nx, ny, storage, monkeypatch):
 
 
 @pytest.mark.parametrize("nx,ny,mask,steps", [
-    (64, 32, 127, 131),     # one graph of 64 steps as 32 pairs, pairs, and an odd last step
+    (64, 32, 127, 131),     # graphs of 128 and 2 steps (as pairs) and an odd last step
     (256, 256, 127, 67),    # the benchmark lattice: 128 tiles of 32 x 16
     (130, 35, 127, 64),     # ragged tiles both ways
     (200, 67, 4 | 8 | 16 | 64, 66),  # masked forces (the general build)
