@@ -217,6 +217,50 @@ def bench_train(steps=20, batch=16, ny=256, nx=256, seed=0):
             "conv_gflop_per_step": flops / 1e9}
 
 
+GEMM_SHAPES = ((8192, 8192, 8192), (4096, 4096, 4096), (65536, 128, 1152), (16384, 64, 576))
+
+
+def bench_gemm(shapes=GEMM_SHAPES, reps=10, seed=0):
+    """The library's tensor-core GEMM (mclbm_gemm_bf16, K-major BF16 operands, FP32 result)
+    against torch.matmul on BF16 (cuBLAS) for shapes (M, N, K): best and median TFLOP/s of each
+    (2 M N K flops per product; CUDA events, 3 untimed calls first) and the relative error of the
+    library's product against an FP32 product of the same BF16 operands."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        ts.sort()
+        return ts[0], ts[len(ts) // 2]
+
+    out = []
+    for M, N, K in shapes:
+        A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
+        Bm = torch.randn(N, K, device="cuda", generator=g).bfloat16()
+        ref = A.float() @ Bm.float().T
+        err = float((gemm_bf16(A, Bm)[0] - ref).norm() / ref.norm())
+        del ref
+        fl = 2.0 * M * N * K
+        ours = timed(lambda: gemm_bf16(A, Bm))
+        lib = timed(lambda: A @ Bm.T)
+        out.append({"M": M, "N": N, "K": K, "rel_err": err,
+                    "tflops": fl / ours[0] / 1e12, "tflops_median": fl / ours[1] / 1e12,
+                    "cublas_tflops": fl / lib[0] / 1e12, "cublas_tflops_median": fl / lib[1] / 1e12})
+        del A, Bm
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---- data, training and evaluation drivers ----------------------------------------------------
 
 def sample_conditions(n, seed):
@@ -390,6 +434,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--bench-train", type=int, default=0,
                     help="only time this many training steps on synthetic targets and exit")
+    ap.add_argument("--bench-gemm", action="store_true",
+                    help="only time the library GEMM against cuBLAS on a few shapes and exit")
     ap.add_argument("--evaluate", default=None,
                     help="only evaluate these weights on --held-out points (seed --seed + 1)")
     ap.add_argument("--plain", action="store_true",
@@ -412,6 +458,10 @@ def main(argv=None):
         return
     if a.bench_train:
         log(json.dumps(bench_train(a.bench_train, ny=a.size, nx=a.size)))
+        return
+    if a.bench_gemm:
+        for r in bench_gemm():
+            log(json.dumps(r))
         return
     if a.evaluate:
         net = WarmNet.load(a.evaluate)
