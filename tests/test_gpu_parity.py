@@ -62,6 +62,20 @@ def test_ragged_and_masked(nx, ny, Ra, phi, d_p, steps, mask):
     _assert_parity(gpu, ref)
 
 
+def test_low_tiles_lattice_2000_steps():
+    """A lattice ragged both ways on which the handle picks the 32 x 7 tiles by itself (9 x 28
+    tiles of 32 x 8 would give some of 152 SMs a second tile; 9 x 32 of 32 x 7 fit two per
+    SM): 2000 steps against the oracle."""
+    import torch
+    gpu, ref = _run_pair(2000, nx=280, ny=220, Ra=1e5, Pr=6.2, phi=0.03, d_p=30e-9, seed=5)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if 252 > sms and 288 <= 2 * sms:
+        k = gpu.step_kernel()
+        assert (k["variant"], k["nodes_per_thread"], k["tile_h"]) == (2, 1, 7), k
+    errs = _assert_parity(gpu, ref)
+    print("low tiles 280 x 220", errs)
+
+
 def test_cavity64_20000_steps():
     gpu, ref = _run_pair(20000, nx=64, ny=64, Ra=1e5, Pr=6.2, phi=0.03, d_p=30e-9, seed=2)
     errs = _assert_parity(gpu, ref)
