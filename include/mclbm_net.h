@@ -63,9 +63,14 @@ int64_t mclbm_net_param_count(const mclbm_net_config* cfg);
  * im2col buffers, gradients); 0 for an invalid configuration. */
 size_t mclbm_net_workspace_bytes(const mclbm_net_config* cfg);
 
-/* Host-only. EINVAL for an invalid configuration. */
+/* A network handle for the configuration (copied). Host-only: no device memory until
+ * mclbm_net_bind. *out is NULL on failure; EINVAL for a NULL out or an invalid configuration. */
 int mclbm_net_create(const mclbm_net_config* cfg, mclbm_net_t** out);
+/* Frees the handle (host memory only; the caller's workspace stays the caller's). NULL is a
+ * no-op. */
 void mclbm_net_destroy(mclbm_net_t* net);
+/* Text of the handle's latest error ("" if none or for a NULL handle); owned by the handle,
+ * valid until its next call. */
 const char* mclbm_net_last_error(const mclbm_net_t* net);
 
 /* Hands over a device workspace of at least mclbm_net_workspace_bytes (256-byte aligned) and
