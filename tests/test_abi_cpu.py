@@ -37,6 +37,27 @@ def test_every_declared_symbol_is_exported(pkg):
     assert set(pkg.EXPORTS) <= decl
 
 
+def test_every_declaration_is_documented():
+    """Each entry point in include/*.h sits under a comment that states what it does (several
+    declarations of one family may share the comment directly above them)."""
+    undocumented = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", fn)).read().split("\n")
+        for k, line in enumerate(lines):
+            m = re.match(r"^[A-Za-z_][\w\s\*]*?\b(mclbm_\w+)\s*\(", line)
+            if not m or line.startswith(("typedef", "#")):
+                continue
+            j = k - 1
+            # skip earlier declarations of the same group (and their continuation lines)
+            while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+                j -= 1
+            if j < 0 or not lines[j].rstrip().endswith("*/"):
+                undocumented.append("%s: %s" % (fn, m.group(1)))
+    assert not undocumented, undocumented
+
+
 def test_props_default(pkg):
     p = pkg.props_default()
     assert p.rho_f == 997.1 and p.rho_p == 3970.0 and p.force_mask == pkg.F_ALL
