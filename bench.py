@@ -39,6 +39,20 @@ WORKLOADS = {"cavity256": workloads.CAVITY_256, "cavity1024": workloads.CAVITY_1
 STEP_SOURCES = ("mclbm_device.cuh", "mclbm_pair.cuh")  # the step kernels' source
 
 
+def step_launches(n):
+    """Kernel launches of mclbm_step(n) on one cavity (the library's decomposition): the even
+    part in graphs of 2^k <= 1024 steps, largest first, each graph one step kernel per step and
+    one epoch kernel; an odd last step as a single launch."""
+    launches, left = 0, n
+    while left >= 2:
+        k = 1
+        while k < 10 and (2 << k) <= left:
+            k += 1
+        launches += (1 << k) + 1
+        left -= 1 << k
+    return launches + left
+
+
 def nodes_per_thread(nx, ny, sms):
     """The step kernel's nodes per thread (the library's rule): one while the lattice gives
     every SM at most two 32 x 8 tiles, two beyond."""
@@ -496,7 +510,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * nx * ny * 4,
                     "d2h_bytes_per_step": 8 * nx * ny * 4 + 16},
-            "gpu_launches": args.steps * (CH + OUR_KERNELS_PER_REDUCTION),
+            "gpu_launches": args.steps * (step_launches(CH) + OUR_KERNELS_PER_REDUCTION),
             "clocks": clk.summary(),
         }
         line.update(extras)

@@ -58,3 +58,16 @@ def test_single_process_aggregation_is_identity():
     import bench
     assert bench.max_over_ranks(3.25, None, "cpu") == 3.25
     assert bench.whole_job_rate(1e6, 1, 2.0) == pytest.approx(0.5)
+
+
+def test_step_launch_count_follows_the_graph_decomposition():
+    """bench.py's gpu_launches: mclbm_step(n) launches n step kernels plus one epoch kernel per
+    captured graph of 2^k steps (k = 1..10, largest first)."""
+    import bench
+    assert bench.step_launches(0) == 0
+    assert bench.step_launches(1) == 1
+    assert bench.step_launches(2) == 3
+    assert bench.step_launches(64) == 65
+    assert bench.step_launches(1000) == 1000 + 6   # 512 + 256 + 128 + 64 + 32 + 8
+    assert bench.step_launches(1001) == 1001 + 6
+    assert bench.step_launches(3000) == 3000 + 8   # 1024 + 1024 + 512 + 256 + 128 + 32 + 16 + 8
