@@ -40,11 +40,14 @@ EXPORTS = ("mclbm_props_default", "mclbm_create", "mclbm_destroy", "mclbm_buffer
 
 
 class NetConfig(C.Structure):
+    """mclbm_net_config (include/mclbm_net.h): grid, base channels, MLP width, largest batch."""
     _fields_ = [("ny", C.c_int32), ("nx", C.c_int32), ("c0", C.c_int32), ("hidden", C.c_int32),
                 ("max_batch", C.c_int32)]
 
 
 class Props(C.Structure):
+    """mclbm_props: material and scale properties, force mask, storage, rounding, thermal
+    sets (field meanings and defaults in include/mclbm.h)."""
     _fields_ = [(n, C.c_double) for n in (
         "rho_f", "cp_f", "k_f", "beta_f", "mu_f", "rho_p", "cp_p", "k_p", "beta_p",
         "T0_K", "dT_K", "g", "l_f", "Ma")] + [("force_mask", C.c_uint32),
@@ -64,10 +67,14 @@ CONST_NAMES = (
 
 
 class Consts(C.Structure):
+    """mclbm_consts: the derived constants of a handle (CONST_NAMES, in order)."""
     _fields_ = [(n, C.c_double) for n in CONST_NAMES]
 
 
 class MclbmError(RuntimeError):
+    """A libmclbm call returned an error code (.code); the message names the call, the code and
+    the handle's last error text."""
+
     def __init__(self, code, what, detail=""):
         super().__init__("%s returned %d (%s)%s" % (
             what, code, _strerror(code), (": " + detail) if detail else ""))
@@ -195,6 +202,7 @@ def _strerror(code):
 
 
 def props_default(**overrides) -> Props:
+    """mclbm_props_default, then the given fields overridden."""
     p = Props()
     lib().mclbm_props_default(C.byref(p))
     for k, v in overrides.items():
@@ -213,6 +221,7 @@ def create(nx, ny, Ra, Pr, phi, d_p, props=None):
 
 
 def get_consts(h) -> dict:
+    """mclbm_get_consts of a handle, as a dict keyed by CONST_NAMES."""
     c = Consts()
     rc = lib().mclbm_get_consts(h, C.byref(c))
     if rc != OK:
@@ -254,6 +263,7 @@ class Cavity:
             raise MclbmError(rc, what, detail)
 
     def close(self):
+        """mclbm_destroy (idempotent); the device buffer goes with the object."""
         if getattr(self, "_h", None):
             lib().mclbm_destroy(self._h)
             self._h = None
@@ -266,12 +276,15 @@ class Cavity:
 
     @property
     def handle(self):
+        """The opaque mclbm_t handle (c_void_p)."""
         return self._h
 
     def consts(self) -> dict:
+        """mclbm_get_consts as a dict."""
         return get_consts(self._h)
 
     def steps_done(self) -> int:
+        """mclbm_steps_done: time steps since the last init or state_set."""
         return int(lib().mclbm_steps_done(self._h))
 
     def step_kernel(self) -> dict:
@@ -301,14 +314,18 @@ class Cavity:
         return self
 
     def step(self, n=1):
+        """mclbm_step: n time steps (async)."""
         self._check(lib().mclbm_step(self._h, int(n)), "mclbm_step")
         return self
 
     def stream_only(self):
+        """mclbm_stream_only: one step of streaming alone (a test hook)."""
         self._check(lib().mclbm_stream_only(self._h), "mclbm_stream_only")
         return self
 
     def fields(self, which, out=None):
+        """mclbm_fields: the selected macroscopic fields (mask of UX, UY, THETA, PHI, ...) as a
+        device float32 tensor [fields][ny][nx], in the order of the mask's bits."""
         k = _nfields(which)
         if out is None:
             out = self.torch.empty((k, self.ny, self.nx), dtype=self.torch.float32,
@@ -328,16 +345,19 @@ class Cavity:
         return self
 
     def nusselt(self):
+        """mclbm_nusselt: (hot-wall, cold-wall) mean Nusselt numbers (syncs)."""
         a, b = C.c_double(), C.c_double()
         self._check(lib().mclbm_nusselt(self._h, C.byref(a), C.byref(b)), "mclbm_nusselt")
         return a.value, b.value
 
     def mass(self):
+        """mclbm_mass: (base fluid, particle) masses (syncs)."""
         a, b = C.c_double(), C.c_double()
         self._check(lib().mclbm_mass(self._h, C.byref(a), C.byref(b)), "mclbm_mass")
         return a.value, b.value
 
     def residual(self):
+        """mclbm_residual: steady-state residual since the previous call (syncs)."""
         r = C.c_double()
         self._check(lib().mclbm_residual(self._h, C.byref(r)), "mclbm_residual")
         return r.value
@@ -351,6 +371,7 @@ class Cavity:
                         (x.value for x in v)))
 
     def state_get(self, out=None):
+        """mclbm_state_get: the population planes [np][ny][nx] (deviations) as float32."""
         if out is None:
             out = self.torch.empty((self.np, self.ny, self.nx), dtype=self.torch.float32,
                                    device=self.device)
@@ -359,6 +380,7 @@ class Cavity:
         return out
 
     def state_set(self, st):
+        """mclbm_state_set: replace the state by the planes of st (layout of state_get)."""
         assert st.dtype == self.torch.float32 and st.is_cuda and st.is_contiguous()
         assert tuple(st.shape) == (self.np, self.ny, self.nx)
         self._check(lib().mclbm_state_set(self._h, C.c_void_p(st.data_ptr())), "mclbm_state_set")
@@ -451,10 +473,12 @@ class Batch:
             raise MclbmError(rc, what, lib().mclbm_batch_last_error(self._h).decode())
 
     def step(self, n):
+        """mclbm_batch_step: n (even) time steps of every active cavity (async)."""
         self._check(lib().mclbm_batch_step(self._h, int(n)), "mclbm_batch_step")
         return self
 
     def nusselt(self):
+        """mclbm_batch_nusselt: hot- and cold-wall Nusselt numbers of every cavity (syncs)."""
         n = len(self.cavities)
         a, b = np.zeros(n), np.zeros(n)
         dp = C.POINTER(C.c_double)
@@ -463,17 +487,21 @@ class Batch:
         return a, b
 
     def set_active(self, active):
+        """mclbm_batch_set_active: only the cavities flagged true keep stepping."""
         arr = (C.c_int * len(self.cavities))(*[1 if x else 0 for x in active])
         self._check(lib().mclbm_batch_set_active(self._h, arr), "mclbm_batch_set_active")
         return self
 
     def tune(self, steps_per_trial=200):
+        """mclbm_batch_tune: times each tile order x CTAs per SM and keeps the fastest;
+        returns (tile order, CTAs per SM)."""
         o, p = C.c_int(), C.c_int()
         self._check(lib().mclbm_batch_tune(self._h, int(steps_per_trial), C.byref(o), C.byref(p)),
                     "mclbm_batch_tune")
         return o.value, p.value
 
     def close(self):
+        """mclbm_batch_destroy (idempotent); the cavities stay usable."""
         if getattr(self, "_h", None):
             lib().mclbm_batch_destroy(self._h)
             self._h = None
